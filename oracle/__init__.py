@@ -1,0 +1,182 @@
+"""CPU oracle for canonical connected-components labelling.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  The GPU library never
+imports it, and it imports nothing from the GPU library.
+
+Result definition (the paper's union-find reaches it exactly):
+  * the paper gives each connected region one unique ID (§I);
+  * its union-find links the larger root under the smaller with atomicMin
+    (§II-A-3), so each component's root is its smallest index;
+  * IDs are global raster indices ``x + y*imgWidth`` (Kernel 1, ID conversion;
+    the Link step of §II-C).
+With ``i = y*W + x``: ``out[i] = 0`` for background, else ``1 + min C(i)``.
+
+Functions
+  * ``label(img, conn)`` -- the C breadth-first flood fill (``ccl_oracle.c``).
+  * ``label_many(imgs, conn)`` -- the same over a stack of equal-size images.
+  * ``label_py(img, conn)`` -- a pure-Python twin for tiny inputs.
+  * ``label_tiles(img, conn, tile_w, tile_h)`` -- each tile labelled as its own
+    image, local indices mapped to global raster indices: the paper's "global
+    label map after local merge" (§II-A-3 ID conversion, Fig. 4(a)).
+  * ``seam_pairs(h, w, conn, tile_w, tile_h)`` -- the cross-tile adjacent pixel
+    pairs the boundary analysis must union (§II-B, Eq. 1-2), enumerated one by
+    one.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from collections import deque
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ccl_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "libccl_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``ccl_oracle.c`` into a shared library with gcc (-O2)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-Wall", "-Wextra", "-shared",
+                           "-fPIC", "-o", tmp, _SRC])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            for name in ("ccl_oracle_bfs",):
+                fn = getattr(lib, name)
+                fn.restype = ctypes.c_int
+                fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                               ctypes.c_int64, ctypes.c_int]
+            fn = lib.ccl_oracle_bfs_many
+            fn.restype = ctypes.c_int
+            fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                           ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
+            _lib = lib
+    return _lib
+
+
+def _check_conn(conn: int) -> None:
+    if conn not in (4, 8):
+        raise ValueError(f"connectivity must be 4 or 8, got {conn}")
+
+
+def label(img: np.ndarray, conn: int = 8) -> np.ndarray:
+    """Canonical labels of a 2-D uint8 image (nonzero = foreground)."""
+    _check_conn(conn)
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    if img.ndim != 2 or img.shape[0] < 1 or img.shape[1] < 1:
+        raise ValueError("img must be a non-empty 2-D array")
+    out = np.empty(img.shape, dtype=np.int32)
+    rc = _load().ccl_oracle_bfs(img.ctypes.data, out.ctypes.data, img.shape[0],
+                                img.shape[1], conn)
+    if rc != 0:
+        raise RuntimeError(f"oracle failed with code {rc}")
+    return out
+
+
+def label_many(imgs: np.ndarray, conn: int = 8) -> np.ndarray:
+    """Canonical labels of a stack ``imgs[k]`` of equal-size 2-D images."""
+    _check_conn(conn)
+    imgs = np.ascontiguousarray(imgs, dtype=np.uint8)
+    if imgs.ndim != 3:
+        raise ValueError("imgs must be (count, h, w)")
+    out = np.empty(imgs.shape, dtype=np.int32)
+    rc = _load().ccl_oracle_bfs_many(imgs.ctypes.data, out.ctypes.data, imgs.shape[0],
+                                     imgs.shape[1], imgs.shape[2], conn)
+    if rc != 0:
+        raise RuntimeError(f"oracle failed with code {rc}")
+    return out
+
+
+def _offsets(conn: int):
+    if conn == 4:
+        return ((1, 0), (-1, 0), (0, 1), (0, -1))
+    return ((1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (1, -1), (-1, 1), (-1, -1))
+
+
+def label_py(img, conn: int = 8) -> np.ndarray:
+    """Pure-Python twin of ``label`` (raster scan + breadth-first flood fill)."""
+    _check_conn(conn)
+    img = np.asarray(img)
+    h, w = img.shape
+    out = np.zeros((h, w), dtype=np.int32)
+    for y0 in range(h):
+        for x0 in range(w):
+            if img[y0, x0] == 0 or out[y0, x0] != 0:
+                continue
+            lab = 1 + y0 * w + x0
+            out[y0, x0] = lab
+            queue = deque([(x0, y0)])
+            while queue:
+                x, y = queue.popleft()
+                for dx, dy in _offsets(conn):
+                    qx, qy = x + dx, y + dy
+                    if 0 <= qx < w and 0 <= qy < h and img[qy, qx] != 0 and out[qy, qx] == 0:
+                        out[qy, qx] = lab
+                        queue.append((qx, qy))
+    return out
+
+
+def label_tiles(img: np.ndarray, conn: int, tile_w: int, tile_h: int) -> np.ndarray:
+    """Label every tile_w x tile_h tile as if it were a separate image.
+
+    A tile's local raster index ``l = ly*tile_w + lx`` of its component root is
+    converted to the global raster index ``(tx*tile_w + lx) + (ty*tile_h + ly)*W``
+    (Kernel 1's local-to-global ID conversion, read with ``lx = l % tile_w``,
+    ``ly = l / tile_w``).  Partial tiles at the right/bottom edge are labelled
+    over their in-image part only.
+    """
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    h, w = img.shape
+    out = np.zeros((h, w), dtype=np.int32)
+    for y0 in range(0, h, tile_h):
+        for x0 in range(0, w, tile_w):
+            sub = img[y0:y0 + tile_h, x0:x0 + tile_w]
+            loc = label(sub, conn).astype(np.int64)
+            sw = sub.shape[1]
+            fg = loc > 0
+            li = loc[fg] - 1
+            ly, lx = li // sw, li % sw
+            glob = np.zeros(sub.shape, dtype=np.int64)
+            glob[fg] = 1 + (y0 + ly) * w + (x0 + lx)
+            out[y0:y0 + tile_h, x0:x0 + tile_w] = glob.astype(np.int32)
+    return out
+
+
+def seam_pairs(h: int, w: int, conn: int, tile_w: int, tile_h: int):
+    """All unordered pairs of in-bounds neighbouring pixels that lie in different
+    tiles, as raster-index tuples ``(p, q)`` with ``p < q`` (pure enumeration).
+
+    These are the cells the boundary analysis (§II-B) works on; Eq. 1-2 count
+    the horizontal/vertical seam cells of a whole-tile grid.
+    """
+    _check_conn(conn)
+    pairs = set()
+    for y in range(h):
+        for x in range(w):
+            for dx, dy in _offsets(conn):
+                qx, qy = x + dx, y + dy
+                if not (0 <= qx < w and 0 <= qy < h):
+                    continue
+                if (x // tile_w, y // tile_h) == (qx // tile_w, qy // tile_h):
+                    continue
+                p, q = y * w + x, qy * w + qx
+                pairs.add((min(p, q), max(p, q)))
+    return pairs

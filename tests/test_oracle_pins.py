@@ -1,0 +1,197 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle is the definition of the result; these tests tie it to things other
+than itself: exhaustive transitive closure on every image up to 4x4,
+hand-worked examples, closed forms, a library routine (scipy.ndimage.label,
+canonicalised), invariants, and an independent two-pass component count.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from helpers import (all_images, canonical_from_arbitrary, check_invariants,
+                     closure_labels, golden_names, load_golden, scipy_canonical,
+                     two_pass_count)
+
+SIZES_4x4 = [(h, w) for h in range(1, 5) for w in range(1, 5)]
+
+
+def test_exhaustive_count():
+    assert sum(1 << (h * w) for h, w in SIZES_4x4) == 74954
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("hw", SIZES_4x4, ids=lambda s: f"{s[0]}x{s[1]}")
+def test_bruteforce_closure_all_images(hw, conn):
+    h, w = hw
+    imgs = all_images(h, w)
+    got = oracle.label_many(imgs, conn)
+    want = closure_labels(imgs, conn)
+    bad = np.nonzero(np.any(got != want, axis=(1, 2)))[0]
+    assert bad.size == 0, f"first mismatch image {bad[:5]}"
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_python_twin_matches_c(conn):
+    imgs = all_images(3, 3)
+    c = oracle.label_many(imgs, conn)
+    for k in range(imgs.shape[0]):
+        np.testing.assert_array_equal(oracle.label_py(imgs[k], conn), c[k])
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        h, w = rng.integers(1, 24, size=2)
+        img = (rng.random((h, w)) < rng.uniform(0.2, 0.8)).astype(np.uint8)
+        np.testing.assert_array_equal(oracle.label_py(img, conn), oracle.label(img, conn))
+
+
+@pytest.mark.parametrize("name", golden_names())
+@pytest.mark.parametrize("conn", [4, 8])
+def test_hand_worked(name, conn):
+    g = load_golden(name)
+    np.testing.assert_array_equal(oracle.label(g["image"], conn), g[f"conn{conn}"])
+    np.testing.assert_array_equal(oracle.label_py(g["image"], conn), g[f"conn{conn}"])
+
+
+def test_hand_worked_tiles():
+    g = load_golden("tiles4.txt")
+    tw, th, want = g["tiles"]
+    for conn in (4, 8):
+        np.testing.assert_array_equal(oracle.label_tiles(g["image"], conn, tw, th), want)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_label_tiles_whole_image_tile(conn):
+    img = synthetic.bernoulli(37, 53, 0.5, 3)
+    np.testing.assert_array_equal(oracle.label_tiles(img, conn, 64, 64), oracle.label(img, conn))
+    # 1x1 tiles: every foreground pixel is its own root
+    idx = np.arange(img.size).reshape(img.shape) + 1
+    np.testing.assert_array_equal(oracle.label_tiles(img, conn, 1, 1), np.where(img > 0, idx, 0))
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("hw", [(1, 1), (1, 7), (7, 1), (5, 9), (64, 64), (33, 17)])
+def test_closed_forms(hw, conn):
+    h, w = hw
+    assert not oracle.label(synthetic.empty(h, w), conn).any()
+    assert np.all(oracle.label(synthetic.full(h, w), conn) == 1)
+    cb = synthetic.checkerboard(h, w)
+    lab = oracle.label(cb, conn)
+    idx = np.arange(h * w).reshape(h, w)
+    if conn == 4 or h == 1 or w == 1:
+        np.testing.assert_array_equal(lab, np.where(cb > 0, idx + 1, 0))
+    else:
+        np.testing.assert_array_equal(lab, cb.astype(np.int32))
+    stripes = np.zeros((h, w), np.uint8)
+    stripes[0::2] = 1
+    ys = np.arange(h)[:, None]
+    want = np.where(stripes > 0, 1 + ys * w, 0)
+    np.testing.assert_array_equal(oracle.label(stripes, conn), want)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("hw", [(8, 8), (9, 13), (64, 40), (257, 131)])
+def test_serpentine_closed_form(hw, conn):
+    h, w = hw
+    for tr in (False, True):
+        img = synthetic.serpentine(h, w, transpose=tr)
+        lab = oracle.label(img, conn)
+        # the path starts at raster index 0 and visits every foreground pixel
+        np.testing.assert_array_equal(lab, img.astype(np.int32))
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_rings_closed_form(conn):
+    h, w = 700, 640
+    img = synthetic.rings(h, w, count=64, spacing=32, inset0=16)
+    lab = oracle.label(img, conn)
+    want = np.zeros((h, w), np.int64)
+    for d in synthetic.ring_insets(h, w):
+        ring = np.zeros((h, w), bool)
+        ring[d, d:w - d] = ring[h - 1 - d, d:w - d] = True
+        ring[d:h - d, d] = ring[d:h - d, w - 1 - d] = True
+        want[ring] = 1 + d * w + d
+    np.testing.assert_array_equal(lab, want)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("hw,count", [((16, 16), 100), ((33, 17), 100), ((64, 64), 100),
+                                      ((128, 96), 100), ((512, 512), 10), ((1024, 1024), 2)])
+def test_scipy_cross_check(hw, count, conn):
+    h, w = hw
+    for seed in range(count):
+        p = [0.1, 0.3, 0.45, 0.5, 0.6, 0.8][seed % 6]
+        img = synthetic.bernoulli(h, w, p, seed, cfg_id=9)
+        np.testing.assert_array_equal(oracle.label(img, conn), scipy_canonical(img, conn))
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_invariants_and_two_pass_count(conn):
+    for seed in range(12):
+        h, w = 40 + seed * 7, 31 + seed * 5
+        p = 0.2 + 0.05 * seed
+        img = synthetic.bernoulli(h, w, p, seed, cfg_id=8)
+        lab = oracle.label(img, conn)
+        check_invariants(img, lab, conn)
+        assert len(np.unique(lab[lab > 0])) == two_pass_count(img, conn)
+
+
+def test_fg_byte_value_irrelevant():
+    img = synthetic.bernoulli(50, 70, 0.5, 1)
+    for conn in (4, 8):
+        np.testing.assert_array_equal(oracle.label(img * 255, conn), oracle.label(img, conn))
+        np.testing.assert_array_equal(oracle.label(img * 7, conn), oracle.label(img, conn))
+
+
+def test_invariants_catch_a_planted_mistake():
+    """A plausible oracle mistake (a dropped diagonal) must trip a pin."""
+    img = load_golden("stairs4.txt")["image"]
+    wrong = oracle.label(img, 4)              # 4-connected result used for 8
+    with pytest.raises(AssertionError):
+        check_invariants(img, wrong, 8)
+    lab = oracle.label(img, 8)
+    bumped = lab.copy()
+    bumped[lab == 3] = 6                      # root index off by a few pixels
+    with pytest.raises(AssertionError):
+        check_invariants(img, bumped, 8)
+
+
+def test_canonicaliser():
+    lab = np.array([[0, 5, 5], [2, 0, 5], [2, 2, 0]])
+    np.testing.assert_array_equal(canonical_from_arbitrary(lab),
+                                  [[0, 2, 2], [4, 0, 2], [4, 4, 0]])
+
+
+def test_oracle_rejects_bad_args():
+    with pytest.raises(ValueError):
+        oracle.label(np.zeros((3, 3), np.uint8), 6)
+    with pytest.raises(ValueError):
+        oracle.label(np.zeros((0, 3), np.uint8), 4)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("hw,tile", [((8, 8), (4, 2)), ((7, 9), (4, 2)), ((12, 10), (3, 5)),
+                                     ((16, 32), (32, 4))])
+def test_seam_pair_closed_form(hw, tile, conn):
+    """Eq. 1-2 count the seam cells of a whole-tile grid; the exact pair count
+    for any size is: all adjacent pairs minus those inside one tile."""
+    h, w = hw
+    tw, th = tile
+    pairs = oracle.seam_pairs(h, w, conn, tw, th)
+    tile_hs = [min(th, h - y) for y in range(0, h, th)]
+    tile_ws = [min(tw, w - x) for x in range(0, w, tw)]
+
+    def pairs4(a, b):
+        return a * (b - 1) + b * (a - 1)
+
+    def diag(a, b):
+        return 2 * max(a - 1, 0) * max(b - 1, 0)
+
+    want = pairs4(h, w) - sum(pairs4(a, b) for a in tile_hs for b in tile_ws)
+    if conn == 8:
+        want += diag(h, w) - sum(diag(a, b) for a in tile_hs for b in tile_ws)
+    assert len(pairs) == want
+    if conn == 4 and h % th == 0 and w % tw == 0:
+        # Eq. 1-2 (with N = width, M = height), minus the image-edge seam they
+        # include: P_x = (W/b_x - 1) * H, P_y = (H/b_y - 1) * W
+        assert len(pairs) == (w // tw - 1) * h + (h // th - 1) * w
