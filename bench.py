@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Benchmark: union-find CCL of an 8192 x 8192 uint8 Bernoulli(p=0.5) image,
+8-connectivity, plain single-image path (``ccl_label``), on N GPUs.
+
+One step = one ``ccl_label`` call (local merge, seam unions, link) on one
+resident 8192^2 image.  Each rank rotates over 3 distinct inputs (and outputs
+and workspaces) so that consecutive steps never find their data in L2
+(3 x (64 MiB in + 256 MiB out) > 129 MB L2).  W warm-up steps, then exactly K
+timed steps bracketed by a barrier and a device synchronise on both sides,
+timed with CUDA events on the launching stream; the max over ranks is used.
+N > 1: independent replicas (images are independent; no collective on the
+data path), weak scaling.
+
+Also reported:
+  roofline      per-kernel CUDA-event time of the dominant kernel (the link
+                kernel, 4 B/px algorithmic) against the measured HBM peak;
+                ``path`` gives the whole step against 5 B/px;
+  e2e           the same metric through the server's C ABI with pinned HOST
+                buffers: host-to-device copy + labelling + device-to-host copy;
+  cpu_baseline  the CPU oracle (single-threaded BFS) on a bounded sample;
+  clocks        nvidia-smi samples taken during the timed region.
+
+``--impl reference`` times the CPU oracle itself as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("Gpixels/s & % HBM roofline (8192² p=0.5, 8-conn); batched/served vs plain, p99")
+UNIT = "Gpixels/s"
+H = W = 8192
+P = 0.5
+CONN = 8
+ROTATE = 3
+FALLBACK_HBM_GBS = 6800.0
+KERNELS = ("local_merge", "seam_union", "link")
+ALG_BYTES_PER_PX = {"local_merge": 1.0, "seam_union": 0.0, "link": 4.0}
+PATH_BYTES_PER_PX = 5.0
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of a float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int, device=None) -> None:
+    if world <= 1:
+        return
+    import torch.distributed as dist
+
+    if device is not None and dist.get_backend() == "nccl":
+        dist.barrier(device_ids=[device.index])
+    else:
+        dist.barrier()
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1708_08180_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d["kernels"][kernel]
+        if d.get("source_hash") != kernel_source_hash():
+            return None
+        return float(ent["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples every 100 ms; keeps those inside [t0, t1]."""
+
+    FIELDS = ("timestamp,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = (bus_id or "").lower()
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [c.strip() for c in line.split(",")]))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0: float, t1: float):
+        rows = [r for (t, r) in self.rows if t0 <= t <= t1 and len(r) >= 10]
+        if self.bus_id:
+            mine = [r for r in rows if self.bus_id.endswith(r[1].lower()[-12:]) or
+                    r[1].lower().endswith(self.bus_id[-12:])]
+            rows = mine or rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        mx = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((num(r[4]) or 0.0) for r in rows)}
+
+
+def cpu_baseline(img, budget_s: float = 15.0):
+    """Time the CPU oracle (as it stands) on the benchmark image, single
+    thread, for about `budget_s` seconds (at least 2 runs)."""
+    import oracle
+
+    oracle.label(img[:64], CONN)                      # build/load outside the timing
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while len(times) < 2 or (time.perf_counter() < t_end and len(times) < 20):
+        t0 = time.perf_counter()
+        oracle.label(img, CONN)
+        times.append(time.perf_counter() - t0)
+    med = statistics.median(times)
+    return {"value": img.size / med / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle BFS on the full {H}x{W} p={P} 8-conn image, {len(times)} runs, "
+                      f"median {med:.3f} s", "runs": len(times)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle as it stands, on host cores, rank 0 only."""
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    import synthetic
+
+    img = synthetic.bernoulli(H, W, P, seed=0)
+    oracle.label(img[:64], CONN)
+    # size each step's sample (whole rows of the benchmark image) so that the
+    # run takes about two minutes in total
+    t0 = time.perf_counter()
+    oracle.label(img[:1024], CONN)
+    px_per_s = 1024 * W / max(time.perf_counter() - t0, 1e-6)
+    total_steps = max(1, args.steps + args.warmup)
+    rows = int(max(1, min(H, 90.0 * px_per_s / total_steps / W)))
+    sample = np.ascontiguousarray(img[:rows])
+    for _ in range(args.warmup):
+        oracle.label(sample, CONN)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.label(sample, CONN)
+    dt = time.perf_counter() - t0
+    value = sample.size * args.steps / dt / 1e9
+    desc = (f"oracle BFS (single thread) on the first {rows} rows ({rows}x{W}) of the "
+            f"{H}x{W} p={P} 8-conn benchmark image per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{H}x{W} uint8 Bernoulli(p={P}), 8-connectivity, CPU oracle",
+                   "sample_rows": rows},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def e2e_server(img_np, steps: int, device_index: int):
+    """Same metric through the server's C ABI with pinned host buffers: every
+    request copies its image host-to-device and its labels device-to-host."""
+    import torch
+
+    import paper_1708_08180_gb300 as ccl
+
+    n = max(4, min(steps, 48))
+    ins = [torch.from_numpy(img_np).pin_memory() for _ in range(2)]
+    window = 6
+    outs = [torch.empty((H, W), dtype=torch.int32).pin_memory() for _ in range(window)]
+    with ccl.Server(conn=CONN, max_batch=1, max_inflight=3, device=device_index) as srv:
+        # warm-up (graph capture, pool growth)
+        for k in range(3):
+            srv.wait(srv.submit(ins[k % 2], outs[k % window]))
+        t0 = time.perf_counter()
+        ids = []
+        for k in range(n):
+            if len(ids) >= window:
+                srv.wait(ids.pop(0))
+            ids.append(srv.submit(ins[k % 2], outs[k % window]))
+        for rid in ids:
+            srv.wait(rid)
+        dt = time.perf_counter() - t0
+        stats = srv.stats()
+    return {"value": n * H * W / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": H * W,
+            "d2h_bytes_per_step": 4 * H * W, "requests": n,
+            "server_p50_ms": stats["p50_ms"], "server_p99_ms": stats["p99_ms"]}
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import paper_1708_08180_gb300 as ccl
+    import synthetic
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    ccl.load()
+
+    host_imgs = [synthetic.bernoulli(H, W, P, seed=rank * ROTATE + r) for r in range(ROTATE)]
+    imgs = [torch.from_numpy(h).to(dev) for h in host_imgs]
+    outs = [torch.empty((H, W), dtype=torch.int32, device=dev) for _ in range(ROTATE)]
+    wsb = ccl.ccl_workspace_bytes(H, W, CONN)
+    wss = [torch.empty(wsb, dtype=torch.uint8, device=dev) for _ in range(ROTATE)]
+    stream = torch.cuda.current_stream(dev)
+
+    for k in range(args.warmup):
+        ccl.ccl_label(imgs[k % ROTATE], CONN, out=outs[k % ROTATE], ws=wss[k % ROTATE],
+                      stream=stream)
+    ccl.ccl_sync(stream)
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+    if bus is not None and not isinstance(bus, str):
+        bus = f"{getattr(props, 'pci_domain_id', 0):08x}:{int(bus):02x}:{getattr(props, 'pci_device_id', 0):02x}.0"
+    sampler = ClockSampler(bus)
+    sampler.start()
+    time.sleep(0.3)
+
+    barrier(world, dev)
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.time()
+    start.record(stream)
+    for k in range(K):
+        ccl.ccl_set_phase_events(ev[k])
+        ccl.ccl_label(imgs[k % ROTATE], CONN, out=outs[k % ROTATE], ws=wss[k % ROTATE],
+                      stream=stream)
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    t_wall1 = time.time()
+    barrier(world, dev)
+    ccl.ccl_sync(stream)
+    sampler.stop()
+
+    ms_local = start.elapsed_time(end)
+    ms_total = reduce_max(ms_local, world, dev)
+    phase = {name: [] for name in KERNELS}
+    for k in range(K):
+        e = ev[k]
+        phase["local_merge"].append(e[0].elapsed_time(e[1]))
+        phase["seam_union"].append(e[1].elapsed_time(e[2]))
+        phase["link"].append(e[2].elapsed_time(e[3]))
+    phase_ms = {n: statistics.mean(v) for n, v in phase.items()}
+    phase_ms = {n: reduce_max(v, world, dev) for n, v in phase_ms.items()}
+    clocks = sampler.summary(t_wall0, t_wall1)
+
+    px = H * W
+    ms_per_step = ms_total / K
+    value = world * px * K / (ms_total / 1e3) / 1e9
+    peak, peak_src = hbm_peak()
+    dominant = max(phase_ms, key=lambda n: phase_ms[n])
+    alg = ALG_BYTES_PER_PX[dominant] * px
+    achieved = alg / (phase_ms[dominant] / 1e3) / 1e9 if phase_ms[dominant] > 0 else 0.0
+    path_gbs = PATH_BYTES_PER_PX * px / (ms_per_step / 1e3) / 1e9
+    traffic = ncu_traffic(dominant)
+    roofline = {
+        "bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1), "peak": peak,
+        "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+        "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+        else "fallback 6.8 TB/s",
+        "algorithmic_bytes_per_launch": alg,
+        "kernel_ms": {n: round(v, 5) for n, v in phase_ms.items()},
+        "path": {"bytes_per_px": PATH_BYTES_PER_PX, "achieved": round(path_gbs, 1),
+                 "frac": round(path_gbs / peak, 4)},
+    }
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{H}x{W} uint8 Bernoulli(p={P}) image, 8-connectivity, plain "
+                               "single-image path (ccl_label), tile 256x64",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": f"{ROTATE} distinct inputs/outputs/workspaces rotated per step "
+                         f"({ROTATE} x 320 MiB > 129 MB L2), no flush"},
+        "roofline": roofline,
+        "gpu_launches": 3 * K,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e_server(host_imgs[0], K, local)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(host_imgs[0])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

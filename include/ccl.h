@@ -1,0 +1,203 @@
+/*
+ * ccl.h -- C ABI of the GB300 (sm_103a) union-find connected-components
+ * labelling library (libccl.so).
+ *
+ * Method: "An Optimized Union-Find Algorithm for Connected Components
+ * Labeling Using GPUs" (Chen et al., 2017).  Three phases over a tiled image:
+ *   1. local merge inside each tile in shared memory (Kernel 1, §II-A),
+ *   2. boundary analysis that unions only across tile seams (Kernel 2, §II-B,
+ *      Eq. 1-2),
+ *   3. link: every pixel receives the root of its component (§II-C).
+ *
+ * Result (canonical form).  For an H x W uint8 image, pixel i = y*W + x is
+ * foreground iff its byte is nonzero.  With 4- (Manhattan-1) or 8-
+ * (Chebyshev-1) adjacency on the foreground pixels,
+ *     labels[i] = 0                          for background,
+ *     labels[i] = 1 + min{ j : j in C(i) }   for foreground,
+ * where C(i) is the component of i.  The paper's union-find links by atomicMin
+ * so every root is its component's smallest index, and its IDs are raster
+ * indices x + y*imgWidth (Kernel 1 ID conversion); "+1, 0 = background" is
+ * this library's encoding.  Results are exact integers and identical for any
+ * tile shape, batch composition or thread interleaving.
+ *
+ * Conventions shared by every call below
+ *   - Images and labels are dense row-major (pitch = width), in DEVICE memory
+ *     owned by the caller, unless a call says "host".
+ *   - 1 <= height, 1 <= width, height*width <= 2^31 - 2 (so 1 + the largest
+ *     index fits in int32).  connectivity is 4 or 8.
+ *   - Calls that take a stream only enqueue work on it and return; a failure
+ *     detected before enqueueing returns an error code and enqueues nothing.
+ *     Device-side failures (a bounded loop that ran out, which valid inputs
+ *     never cause) are recorded in a per-device error word reported by
+ *     ccl_sync().
+ *   - Workspace: scratch device memory, caller-owned when given.  Its size
+ *     comes from the matching *_workspace_bytes() call and it must be 256-byte
+ *     aligned.  Passing NULL makes the library use its own per-(device,
+ *     stream) buffer (grown on demand with cudaMalloc, which synchronises the
+ *     device; released by ccl_shutdown()).  Two calls in flight at once on
+ *     different streams must not share one caller workspace.
+ *   - No call throws; all report through ccl_status.
+ */
+#ifndef CCL_H
+#define CCL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CCL_OK = 0,
+    CCL_ERR_INVALID_ARG = 1, /* bad size, connectivity, pointer or workspace */
+    CCL_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    CCL_ERR_OOM = 3,         /* device or host allocation failed */
+    CCL_ERR_TIMEOUT = 4,     /* a bounded wait/loop ran out (device error word) */
+    CCL_ERR_REJECTED = 5,    /* server: request larger than the whole budget */
+    CCL_ERR_SHUTDOWN = 6,    /* server: destroyed or shutting down */
+    CCL_ERR_NOT_FOUND = 7,   /* server: unknown request id */
+    CCL_ERR_PENDING = 8      /* server: request not finished yet (poll) */
+} ccl_status;
+
+/* Opaque CUDA stream handle (cudaStream_t); NULL = the legacy default stream. */
+typedef void *ccl_stream;
+
+/* Human-readable name of a status code; never NULL, static storage. */
+const char *ccl_status_string(int status);
+
+/* ------------------------------------------------------------------------ */
+/* Single image                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Tile widths the kernels support: 32, 64, 128 or 256 pixels.  A tile always
+ * holds 256 strips x words; its height is (8192 / tile_w) rows for
+ * 4-connectivity and twice that for 8-connectivity.  0 = library default
+ * for the image size (the autotuned table). */
+int ccl_default_tile_width(int height, int width, int connectivity);
+
+/* Bytes of workspace ccl_label / ccl_label_tiled need for this image and tile
+ * width (tile_w 0 = default).  0 on invalid arguments. */
+size_t ccl_workspace_bytes(int height, int width, int connectivity);
+size_t ccl_workspace_bytes_tiled(int height, int width, int connectivity, int tile_w);
+
+/* Label one image (all three phases: local merge §II-A, boundary analysis
+ * §II-B, link §II-C) with the default tile width.
+ *   d_img    : device, height*width bytes, nonzero = foreground (read only)
+ *   d_labels : device, height*width int32, fully overwritten (the link phase
+ *              also uses it as the global union-find array, so it must not
+ *              alias d_img or the workspace)
+ *   d_ws     : device workspace of ws_bytes >= ccl_workspace_bytes(), or NULL
+ *   stream   : CUDA stream to enqueue on
+ * Returns CCL_OK once the three kernels are enqueued. */
+ccl_status ccl_label(const uint8_t *d_img, int32_t *d_labels, int height, int width,
+                     int connectivity, void *d_ws, size_t ws_bytes, ccl_stream stream);
+
+/* Flags for ccl_label_tiled. */
+#define CCL_FLAG_LOCAL_ONLY 1u /* stop after the local merge: every tile is
+                                  labelled as if it were a separate image and
+                                  its root index converted to the global raster
+                                  index (Kernel 1 output, the paper's "global
+                                  label map after local merge", Fig. 4(a)) */
+
+/* As ccl_label with an explicit tile width (32, 64, 128, 256; 0 = default)
+ * and flags.  Same arguments, ownership and errors as ccl_label. */
+ccl_status ccl_label_tiled(const uint8_t *d_img, int32_t *d_labels, int height, int width,
+                           int connectivity, int tile_w, unsigned flags, void *d_ws,
+                           size_t ws_bytes, ccl_stream stream);
+
+/* Number of unordered pairs of neighbouring pixels that lie in different
+ * tiles for this size, connectivity and tile (tile_w x tile_h): the cells the
+ * boundary analysis inspects (§II-B; Eq. 1-2 count them for a whole-tile grid).
+ * Host-only arithmetic; -1 on invalid arguments. */
+long long ccl_seam_pair_count(int height, int width, int connectivity, int tile_w,
+                              int tile_h);
+
+/* Benchmark hook: when `events` is non-NULL, the next ccl_label /
+ * ccl_label_tiled call made by this host thread records events[0] before its
+ * local-merge kernel, events[1] after it, events[2] after the seam-union
+ * kernel and events[3] after the link kernel, all on that call's stream.
+ * `events` points to 4 caller-owned cudaEvent_t handles (created with timing
+ * enabled); the hook is consumed by that one call.  NULL clears it. */
+void ccl_set_phase_events(void *const *events);
+
+/* Wait for `stream`, then report and clear the device error word of the
+ * current device: CCL_OK, CCL_ERR_TIMEOUT, or CCL_ERR_CUDA for an
+ * asynchronous CUDA error. */
+ccl_status ccl_sync(ccl_stream stream);
+
+/* Free library-owned workspaces and batched-path state on every device. */
+ccl_status ccl_shutdown(void);
+
+/* ------------------------------------------------------------------------ */
+/* Batched: many images of different sizes in one launch sequence           */
+/* ------------------------------------------------------------------------ */
+
+/* One image of a batch: device pointers, caller-owned. */
+typedef struct {
+    const uint8_t *d_img;
+    int32_t *d_labels;
+    int height;
+    int width;
+} ccl_image;
+
+/* Workspace bytes for a batch (descriptor table, tile work list and per-image
+ * scratch).  0 on invalid arguments. */
+size_t ccl_batched_workspace_bytes(const ccl_image *imgs, int n, int connectivity);
+
+/* Label n images (host array of descriptors; the images themselves are on the
+ * device) with one pass of three persistent kernels that pull tiles of all
+ * images from a device work queue; each image's tile width comes from the
+ * size-class table (ccl_default_tile_width).  The descriptor table is copied
+ * to the workspace with one host-to-device copy on `stream`, so `imgs` may be
+ * reused as soon as the call returns.  Per-image results equal ccl_label's
+ * exactly.  n >= 1; every image obeys the single-image limits. */
+ccl_status ccl_label_batched(const ccl_image *imgs, int n, int connectivity, void *d_ws,
+                             size_t ws_bytes, ccl_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Server: continuous batching of host-memory requests                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    size_t hbm_budget_bytes; /* device bytes requests in flight may hold; 0 = 40 GB */
+    int max_batch;           /* most images per batched launch; 0 = 256 */
+    int max_inflight;        /* batches in flight at once (>= 1); 0 = 2 */
+    int connectivity;        /* 4 or 8 */
+    int device;              /* CUDA device ordinal */
+} ccl_server_config;
+
+typedef struct ccl_server ccl_server;
+
+/* Start a server: worker thread, streams and pinned staging on `device`. */
+ccl_status ccl_server_create(const ccl_server_config *cfg, ccl_server **out);
+
+/* Queue one request (non-blocking).  h_img (height*width bytes) and
+ * h_labels_out (height*width int32) are HOST buffers owned by the caller that
+ * must stay valid until ccl_server_wait/poll reports completion.  A request
+ * larger than the whole budget returns CCL_ERR_REJECTED; smaller ones wait
+ * until enough budget is free.  *req_id_out receives the request id. */
+ccl_status ccl_server_submit(ccl_server *srv, const uint8_t *h_img, int height, int width,
+                             int32_t *h_labels_out, uint64_t *req_id_out);
+
+/* Block until request `req_id` finished (its labels are in h_labels_out) or
+ * timeout_ms passed (CCL_ERR_TIMEOUT; < 0 waits forever).  Returns the
+ * request's own status once finished. */
+ccl_status ccl_server_wait(ccl_server *srv, uint64_t req_id, int timeout_ms);
+
+/* Non-blocking: CCL_ERR_PENDING while the request is queued or running. */
+ccl_status ccl_server_poll(ccl_server *srv, uint64_t req_id);
+
+/* Statistics since creation: latency percentiles in ms (submit -> labels in
+ * host memory), Gpixel/s of completed work over the busy interval, counts. */
+ccl_status ccl_server_stats(ccl_server *srv, double *p50_ms, double *p99_ms,
+                            double *gpix_per_s, uint64_t *completed, uint64_t *rejected);
+
+/* Stop accepting, finish every admitted request, release all resources. */
+ccl_status ccl_server_destroy(ccl_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCL_H */

@@ -1,0 +1,266 @@
+"""GB300-native union-find connected-components labelling (CCL).
+
+Python binding over the C ABI of ``libccl.so`` (``include/ccl.h``): argument
+marshalling only -- every step of the labelling runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.
+
+    >>> import torch, paper_1708_08180_gb300 as ccl
+    >>> img = (torch.rand(1024, 1024, device="cuda") < 0.5).to(torch.uint8)
+    >>> labels = ccl.label(img, conn=8)   # int32, 0 = background,
+    ...                                   # 1 + smallest raster index of the component
+
+Functions named ``ccl_*`` mirror the C entry points one to one.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Iterable, List, Optional, Sequence
+
+from ._lib import (CCL_ERR_PENDING, CCL_ERR_TIMEOUT, CCL_FLAG_LOCAL_ONLY, CCL_OK, CclError,
+                   ccl_image, ccl_server_config, check, load, status_string)
+
+__all__ = [
+    "CclError", "CCL_FLAG_LOCAL_ONLY", "label", "label_batched", "ccl_label", "ccl_label_tiled",
+    "ccl_label_batched", "ccl_workspace_bytes", "ccl_workspace_bytes_tiled",
+    "ccl_batched_workspace_bytes", "ccl_default_tile_width", "ccl_seam_pair_count", "ccl_sync",
+    "ccl_shutdown", "ccl_status_string", "ccl_set_phase_events", "Server", "load",
+]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_handle(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _check_img(img):
+    torch = _torch()
+    if not isinstance(img, torch.Tensor) or not img.is_cuda:
+        raise TypeError("image must be a CUDA tensor")
+    if img.dtype != torch.uint8 or img.dim() != 2 or not img.is_contiguous():
+        raise TypeError("image must be a contiguous 2-D uint8 tensor")
+
+
+def ccl_status_string(status: int) -> str:
+    return status_string(status)
+
+
+def ccl_default_tile_width(height: int, width: int, conn: int) -> int:
+    return int(load().ccl_default_tile_width(height, width, conn))
+
+
+def ccl_workspace_bytes(height: int, width: int, conn: int) -> int:
+    return int(load().ccl_workspace_bytes(height, width, conn))
+
+
+def ccl_workspace_bytes_tiled(height: int, width: int, conn: int, tile_w: int) -> int:
+    return int(load().ccl_workspace_bytes_tiled(height, width, conn, tile_w))
+
+
+def ccl_seam_pair_count(height: int, width: int, conn: int, tile_w: int, tile_h: int) -> int:
+    return int(load().ccl_seam_pair_count(height, width, conn, tile_w, tile_h))
+
+
+def _workspace(nbytes: int, device):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def ccl_label_tiled(img, conn: int = 8, tile_w: int = 0, flags: int = 0, out=None, ws=None,
+                    stream=None):
+    """Label ``img`` (CUDA uint8, H x W) into ``out`` (CUDA int32, H x W).
+
+    ``ws``: a CUDA uint8 tensor of at least ``ccl_workspace_bytes_tiled`` bytes
+    (allocated here when None).  Enqueued on ``stream`` (default: current)."""
+    torch = _torch()
+    _check_img(img)
+    h, w = img.shape
+    if out is None:
+        out = torch.empty((h, w), dtype=torch.int32, device=img.device)
+    elif out.dtype != torch.int32 or tuple(out.shape) != (h, w) or not out.is_contiguous():
+        raise TypeError("out must be a contiguous int32 tensor shaped like img")
+    need = ccl_workspace_bytes_tiled(h, w, conn, tile_w)
+    if need == 0:
+        raise CclError(1, "ccl_workspace_bytes_tiled")
+    if ws is None:
+        ws = _workspace(need, img.device)
+    with torch.cuda.device(img.device):
+        st = load().ccl_label_tiled(img.data_ptr(), out.data_ptr(), h, w, conn, tile_w, flags,
+                                    ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    check(st, "ccl_label_tiled")
+    return out
+
+
+def ccl_label(img, conn: int = 8, out=None, ws=None, stream=None):
+    """Label one image with the default tile shape (see ``ccl_label_tiled``)."""
+    torch = _torch()
+    _check_img(img)
+    h, w = img.shape
+    if out is None:
+        out = torch.empty((h, w), dtype=torch.int32, device=img.device)
+    need = ccl_workspace_bytes(h, w, conn)
+    if need == 0:
+        raise CclError(1, "ccl_workspace_bytes")
+    if ws is None:
+        ws = _workspace(need, img.device)
+    with torch.cuda.device(img.device):
+        st = load().ccl_label(img.data_ptr(), out.data_ptr(), h, w, conn, ws.data_ptr(),
+                              ws.numel(), _stream_handle(stream))
+    check(st, "ccl_label")
+    return out
+
+
+def _image_array(imgs, outs):
+    arr = (ccl_image * len(imgs))()
+    for k, (im, o) in enumerate(zip(imgs, outs)):
+        arr[k].d_img = im.data_ptr()
+        arr[k].d_labels = o.data_ptr()
+        arr[k].height = im.shape[0]
+        arr[k].width = im.shape[1]
+    return arr
+
+
+def ccl_batched_workspace_bytes(shapes: Sequence, conn: int = 8) -> int:
+    """Workspace bytes for a batch given ``[(h, w), ...]`` or tensors."""
+    arr = (ccl_image * len(shapes))()
+    for k, s in enumerate(shapes):
+        h, w = (s.shape if hasattr(s, "shape") else s)
+        arr[k].d_img = 256
+        arr[k].d_labels = 256
+        arr[k].height, arr[k].width = int(h), int(w)
+    return int(load().ccl_batched_workspace_bytes(arr, len(shapes), conn))
+
+
+def ccl_label_batched(imgs: Sequence, conn: int = 8, outs: Optional[Sequence] = None, ws=None,
+                      stream=None) -> List:
+    """Label a list of CUDA uint8 images of any sizes in one batched launch."""
+    torch = _torch()
+    if len(imgs) == 0:
+        return []
+    for im in imgs:
+        _check_img(im)
+    dev = imgs[0].device
+    if outs is None:
+        outs = [torch.empty(tuple(im.shape), dtype=torch.int32, device=im.device) for im in imgs]
+    arr = _image_array(imgs, outs)
+    need = int(load().ccl_batched_workspace_bytes(arr, len(imgs), conn))
+    if need == 0:
+        raise CclError(1, "ccl_batched_workspace_bytes")
+    if ws is None:
+        ws = _workspace(need, dev)
+    with torch.cuda.device(dev):
+        st = load().ccl_label_batched(arr, len(imgs), conn, ws.data_ptr(), ws.numel(),
+                                      _stream_handle(stream))
+    check(st, "ccl_label_batched")
+    return list(outs)
+
+
+def ccl_sync(stream=None) -> None:
+    """Wait for ``stream`` and raise if a device-side bounded loop ran out."""
+    check(load().ccl_sync(_stream_handle(stream)), "ccl_sync")
+
+
+def ccl_set_phase_events(events) -> None:
+    """Arm the per-kernel timing hook for this thread's next ccl_label call:
+    ``events`` is 4 ``torch.cuda.Event(enable_timing=True)`` (or None)."""
+    if events is None:
+        load().ccl_set_phase_events(None)
+        return
+    arr = (ctypes.c_void_p * 4)(*[int(e.cuda_event) for e in events])
+    load().ccl_set_phase_events(arr)
+
+
+def ccl_shutdown() -> None:
+    check(load().ccl_shutdown(), "ccl_shutdown")
+
+
+def label(img, conn: int = 8, tile_w: int = 0):
+    """Canonical labels of a CUDA uint8 image (blocking convenience wrapper)."""
+    out = ccl_label_tiled(img, conn, tile_w)
+    ccl_sync()
+    return out
+
+
+def label_batched(imgs: Iterable, conn: int = 8):
+    outs = ccl_label_batched(list(imgs), conn)
+    ccl_sync()
+    return outs
+
+
+class Server:
+    """Continuous-batching server over host buffers (``ccl_server_*``).
+
+    ``submit`` takes a contiguous host uint8 array/tensor and a host int32
+    output of the same shape (pinned memory recommended); both must stay alive
+    until ``wait``/``poll`` reports completion."""
+
+    def __init__(self, conn: int = 8, hbm_budget_bytes: int = 0, max_batch: int = 0,
+                 max_inflight: int = 0, device: int = 0):
+        cfg = ccl_server_config(hbm_budget_bytes, max_batch, max_inflight, conn, device)
+        h = ctypes.c_void_p()
+        check(load().ccl_server_create(ctypes.byref(cfg), ctypes.byref(h)), "ccl_server_create")
+        self._h = h
+        self._keep = {}
+
+    @staticmethod
+    def _ptr(a):
+        if hasattr(a, "data_ptr"):
+            return a.data_ptr()
+        return a.ctypes.data
+
+    def submit(self, img, out) -> int:
+        h, w = img.shape
+        rid = ctypes.c_uint64()
+        st = load().ccl_server_submit(self._h, self._ptr(img), h, w, self._ptr(out),
+                                      ctypes.byref(rid))
+        check(st, "ccl_server_submit")
+        self._keep[rid.value] = (img, out)
+        return rid.value
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> None:
+        st = load().ccl_server_wait(self._h, rid, timeout_ms)
+        if st != CCL_ERR_TIMEOUT:
+            self._keep.pop(rid, None)
+        check(st, "ccl_server_wait")
+
+    def poll(self, rid: int) -> bool:
+        st = load().ccl_server_poll(self._h, rid)
+        if st == CCL_ERR_PENDING:
+            return False
+        self._keep.pop(rid, None)
+        check(st, "ccl_server_poll")
+        return True
+
+    def stats(self) -> dict:
+        p50, p99, gp = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        done, rej = ctypes.c_uint64(), ctypes.c_uint64()
+        check(load().ccl_server_stats(self._h, ctypes.byref(p50), ctypes.byref(p99),
+                                      ctypes.byref(gp), ctypes.byref(done), ctypes.byref(rej)),
+              "ccl_server_stats")
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "gpix_per_s": gp.value,
+                "completed": done.value, "rejected": rej.value}
+
+    def close(self) -> None:
+        if self._h:
+            check(load().ccl_server_destroy(self._h), "ccl_server_destroy")
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,271 @@
+// ccl_core.cuh -- device building blocks of the three-phase union-find CCL
+// for sm_103a: bit-packed rows, segment ("run") nodes, shared-memory and
+// global-memory union-find, tile geometry and per-tile workspace layout.
+//
+// Phases (Chen et al., "An Optimized Union-Find Algorithm for Connected
+// Components Labeling Using GPUs"):
+//   local merge     Kernel 1, §II-A: each thread block labels one tile in
+//                   shared memory, roots converted to global raster indices;
+//   boundary        Kernel 2, §II-B, Eq. 1-2: unions only across tile seams;
+//   link            §II-C: every pixel gets the root of its component.
+//
+// GB300 design (what differs from the paper's per-pixel Pascal kernels):
+//   * A pixel is one bit.  A thread owns one 32-pixel word of a tile row (two
+//     rows for 8-connectivity) and finds run starts with shifts, so the
+//     paper's row scan and coarse row-column unification (§II-A-2) become a
+//     handful of integer instructions per 32 pixels.
+//   * Union-find nodes are *segments*: maximal runs of a row (4-connectivity)
+//     or of the OR of a two-row strip (8-connectivity: within two rows, all
+//     pixels of consecutive non-empty columns are 8-connected).  Unions are
+//     needed only between consecutive strips, one per touching run pair.
+//   * Roots stay the smallest raster index, as with the paper's atomicMin
+//     linking (§II-A-3), but the link step uses the value returned by the
+//     atomic (a compare-and-swap that fails when the root was linked
+//     concurrently) so a concurrent link is never lost.
+//   * The link phase does not re-run union-find: the local merge stores one
+//     label per segment (compact) plus the bit-packed image, and the link
+//     kernel re-derives segments from the bits.  HBM traffic is about
+//     1 B/px read + 4 B/px written plus ~0.6 B/px of compact scratch.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ccl {
+
+constexpr int kThreads = 256;             // threads per tile = strips x words
+constexpr int kNodeCap = kThreads * 16;   // at most 16 run starts per 32-bit word
+constexpr int kBorderCapMax = 576;        // border segments: <= 2*16*NW + 2*NS for every NW
+constexpr int kHdrInts = 4;               // [0] = border-root count
+
+constexpr int kKeyFlag = 0x40000000;      // "component touches a tile seam"
+constexpr int kKeyMask = 0x3FFFFFFF;
+constexpr uint32_t kEncBit = 0x80000000u; // parent pointers in the global array
+
+// device error word bits
+constexpr int kErrSmemFind = 1;
+constexpr int kErrSmemUnion = 2;
+constexpr int kErrGlobFind = 4;
+constexpr int kErrGlobUnion = 8;
+constexpr int kErrResolve = 16;
+constexpr int kErrBorderCap = 32;
+constexpr int kErrQueue = 64;
+
+constexpr int kSmemLoopCap = 1 << 16;
+constexpr int kGlobLoopCap = 1 << 26;
+
+// Geometry of one image under one tile shape, and the layout of the per-tile
+// workspace (all offsets in ints from the tile's base):
+//   [0, kHdrInts)                header: [0] = number of border roots
+//   [kHdrInts, off_border)       label of each segment node (node_cap)
+//   [off_border, off_rec)        global index of each border root (border_cap)
+//   [off_rec, off_rec + rec)     seam records: top[tw], bottom[tw], left[ns], right[ns]
+struct Geom {
+    int H, W;
+    int nw;         // 32-bit words per tile row: 1, 2, 4, 8
+    int ns;         // strips per tile = kThreads / nw
+    int hs;         // strip height: 1 (4-conn) or 2 (8-conn)
+    int tw, th;     // tile width / height in pixels
+    int log2tw;
+    int tiles_x, tiles_y;
+    int nwg;        // words per bit-image row = ceil(W / 32)
+    int node_cap;   // most segment nodes a tile of this image can hold
+    int border_cap; // most border roots
+    int off_border, off_rec, tile_ints;
+};
+
+__host__ __device__ inline Geom make_geom(int H, int W, int conn, int tile_w) {
+    Geom g;
+    g.H = H;
+    g.W = W;
+    g.nw = tile_w / 32;
+    g.ns = kThreads / g.nw;
+    g.hs = conn == 8 ? 2 : 1;
+    g.tw = tile_w;
+    g.th = g.ns * g.hs;
+    g.log2tw = tile_w == 32 ? 5 : tile_w == 64 ? 6 : tile_w == 128 ? 7 : 8;
+    g.tiles_x = (W + g.tw - 1) / g.tw;
+    g.tiles_y = (H + g.th - 1) / g.th;
+    g.nwg = (W + 31) / 32;
+    // a strip row of c valid columns holds at most ceil(c / 2) runs
+    const int cols = W < g.tw ? W : g.tw;
+    const int per_strip = (cols + 1) / 2;
+    g.node_cap = g.ns * per_strip;
+    g.border_cap = 2 * per_strip + 2 * g.ns;
+    g.off_border = kHdrInts + g.node_cap;
+    g.off_rec = g.off_border + g.border_cap;
+    g.tile_ints = (g.off_rec + 2 * g.tw + 2 * g.ns + 63) & ~63;   // 256-byte multiple
+    return g;
+}
+
+__host__ __device__ inline size_t bits_bytes(const Geom &g) {
+    size_t b = (size_t)g.H * (size_t)g.nwg * 4u;
+    return (b + 255u) & ~(size_t)255u;
+}
+
+__host__ __device__ inline size_t tiles_bytes(const Geom &g) {
+    return (size_t)g.tiles_x * (size_t)g.tiles_y * (size_t)g.tile_ints * 4u;
+}
+
+// ---------------------------------------------------------------------------
+// bit helpers
+
+// mask of bits 0..x (x in [-1, 31]); x = -1 gives 0
+__device__ __forceinline__ uint32_t le_mask(int x) {
+    return x < 0 ? 0u : (0xFFFFFFFFu >> (31 - x));
+}
+
+// 4-bit mask of the nonzero bytes of v (byte k -> bit k): the high bit of
+// ((b & 0x7f) + 0x7f) | b is set iff b != 0; the multiply gathers the four
+// high bits (positions 7, 15, 23, 31 after >>7: 0, 8, 16, 24) into bits 28-31
+// with no carries between partial products.
+__device__ __forceinline__ uint32_t nz4(uint32_t v) {
+    uint32_t x = (((v & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | v) & 0x80808080u;
+    return ((x >> 7) * 0x10204080u) >> 28;
+}
+
+__device__ __forceinline__ uint32_t nz16(uint4 v) {
+    return nz4(v.x) | (nz4(v.y) << 4) | (nz4(v.z) << 8) | (nz4(v.w) << 12);
+}
+
+// Foreground bits of pixels [gx, gx + n) of row y (n = min(32, W - gx)),
+// bit k = pixel gx + k.  img_end bounds every byte read.
+__device__ __forceinline__ uint32_t load_row_bits(const uint8_t *__restrict__ img,
+                                                  const uint8_t *img_end, int y, int gx,
+                                                  int W, bool aligned16) {
+    int n = W - gx;
+    if (n > 32) n = 32;
+    const uint8_t *p = img + (size_t)y * (size_t)W + (size_t)gx;
+    if (aligned16) {
+        // W % 16 == 0 and 16-byte aligned base: n is 16 or 32
+        uint32_t bits = nz16(__ldg(reinterpret_cast<const uint4 *>(p)));
+        if (n > 16) bits |= nz16(__ldg(reinterpret_cast<const uint4 *>(p + 16))) << 16;
+        return bits;
+    }
+    uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    int off = (int)(a & 3u);
+    const uint8_t *wb = p - off;
+    int nwords = (off + n + 3) >> 2;
+    uint64_t acc = 0;
+    for (int k = 0; k < nwords; ++k) {
+        const uint8_t *q = wb + 4 * k;
+        uint32_t m4;
+        if (q >= img && q + 4 <= img_end) {
+            m4 = nz4(__ldg(reinterpret_cast<const uint32_t *>(q)));
+        } else {
+            m4 = 0;
+            for (int b = 0; b < 4; ++b)
+                if (q + b >= img && q + b < img_end && q[b] != 0) m4 |= 1u << b;
+        }
+        acc |= (uint64_t)m4 << (4 * k);
+    }
+    uint32_t bits = (uint32_t)(acc >> off);
+    return n == 32 ? bits : (bits & ((1u << n) - 1u));
+}
+
+// ---------------------------------------------------------------------------
+// block-wide exclusive scan over kThreads threads (tid order)
+
+__device__ __forceinline__ int block_excl_scan(int v, int *warp_sums, int &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int s = lane < kThreads / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < kThreads / 32; o <<= 1) {
+            int y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kThreads / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    total = warp_sums[kThreads / 32 - 1];
+    return x - v + (warp > 0 ? warp_sums[warp - 1] : 0);
+}
+
+// ---------------------------------------------------------------------------
+// union-find in shared memory over segment nodes.  P[n] = parent (P[n] <= n is
+// not required: links go from the root with the larger key to the one with
+// the smaller key, so every root is the smallest key of its tree).
+
+__device__ __forceinline__ int sfind(volatile int *P, int x, int *err) {
+    for (int it = 0; it < kSmemLoopCap; ++it) {
+        int p = P[x];
+        if (p == x) return x;
+        int g = P[p];
+        if (g == p) return p;
+        P[x] = g;   // path halving: g is an ancestor of x
+        x = g;
+    }
+    atomicOr(err, kErrSmemFind);
+    return x;
+}
+
+__device__ __forceinline__ void sunion(int *P, const int *K, int a, int b, int *err) {
+    volatile int *vP = P;
+    volatile const int *vK = K;
+    for (int it = 0; it < kSmemLoopCap; ++it) {
+        a = sfind(vP, a, err);
+        b = sfind(vP, b, err);
+        if (a == b) return;
+        if ((vK[a] & kKeyMask) > (vK[b] & kKeyMask)) { int t = a; a = b; b = t; }
+        // link root b (larger key) under root a; fails if b stopped being a root
+        if (atomicCAS(&P[b], b, a) == b) return;
+    }
+    atomicOr(err, kErrSmemUnion);
+}
+
+// ---------------------------------------------------------------------------
+// union-find in global memory over raster indices (keys), stored in the label
+// buffer itself: G[x] = x | kEncBit is a parent pointer (negative as int32),
+// a value >= 0 is a final label (only written by the link phase).
+
+__device__ __forceinline__ int gload(const int *p) { return __ldcg(p); }
+
+__device__ __forceinline__ int gfind(int *G, int x, int *err) {
+    for (int it = 0; it < kGlobLoopCap; ++it) {
+        int p = (int)((uint32_t)gload(G + x) & ~kEncBit);
+        if (p == x) return x;
+        int g = (int)((uint32_t)gload(G + p) & ~kEncBit);
+        if (g == p) return p;
+        __stcg(G + x, (int)((uint32_t)g | kEncBit));   // path halving
+        x = g;
+    }
+    atomicOr(err, kErrGlobFind);
+    return x;
+}
+
+__device__ __forceinline__ void gunion(int *G, int a, int b, int *err) {
+    for (int it = 0; it < kGlobLoopCap; ++it) {
+        a = gfind(G, a, err);
+        b = gfind(G, b, err);
+        if (a == b) return;
+        if (a > b) { int t = a; a = b; b = t; }
+        const int eb = (int)((uint32_t)b | kEncBit), ea = (int)((uint32_t)a | kEncBit);
+        if (atomicCAS(G + b, eb, ea) == eb) return;
+    }
+    atomicOr(err, kErrGlobUnion);
+}
+
+// Read-only root lookup for the link phase: follows parent pointers until a
+// root (label 1 + root) or a node whose owner already wrote its final label.
+__device__ __forceinline__ int gresolve(const int *G, int x, int *err) {
+    for (int it = 0; it < kGlobLoopCap; ++it) {
+        int v = gload(G + x);
+        if (v >= 0) return v;
+        int p = (int)((uint32_t)v & ~kEncBit);
+        if (p == x) return x + 1;
+        x = p;
+    }
+    atomicOr(err, kErrResolve);
+    return 0;
+}
+
+}  // namespace ccl

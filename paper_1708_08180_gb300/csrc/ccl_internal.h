@@ -1,0 +1,34 @@
+// ccl_internal.h -- host-side helpers shared by the library's translation
+// units (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/ccl.h"
+
+namespace ccl {
+
+// Device address of the current device's error word (set up once per device).
+int *device_error_word();
+
+// Library-owned workspace for (current device, stream), grown to >= bytes.
+void *library_workspace(cudaStream_t stream, size_t bytes, ccl_status *st);
+
+// Release every library-owned workspace.
+void free_library_workspaces();
+
+// Argument checks shared by the entry points.
+bool valid_image_dims(int height, int width);
+inline bool valid_conn(int conn) { return conn == 4 || conn == 8; }
+inline bool valid_tile_w(int tw) { return tw == 32 || tw == 64 || tw == 128 || tw == 256; }
+
+// Size-class table: tile width for an image (the autotuned default).
+int default_tile_width(int height, int width, int conn);
+
+// Release batched-path state.
+void free_batched_state();
+
+}  // namespace ccl

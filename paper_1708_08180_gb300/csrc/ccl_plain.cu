@@ -1,0 +1,145 @@
+// ccl_plain.cu -- single-image path: the three kernels (local merge, seam
+// unions, link) and the ccl_label / ccl_label_tiled entry points.
+#include "ccl_internal.h"
+#include "ccl_tile.cuh"
+
+namespace ccl {
+
+template <int NW, int HS>
+__global__ void __launch_bounds__(kThreads) k_merge(ImageArgs a, int local_only, int *err) {
+    __shared__ SmemMerge sm;
+    merge_tile<NW, HS>(a, blockIdx.x, local_only != 0, sm, err);
+}
+
+__global__ void __launch_bounds__(256) k_seams(ImageArgs a, long long nitems, int *err) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < nitems) seam_item(a, idx, err);
+}
+
+template <int NW, int HS>
+__global__ void __launch_bounds__(kThreads) k_link(ImageArgs a, int *err) {
+    __shared__ SmemLink sm;
+    link_tile<NW, HS>(a, blockIdx.x, sm, err);
+}
+
+template <int NW, int HS>
+static void launch_merge_link(const ImageArgs &a, bool local_only, int *err, cudaStream_t s,
+                              bool link) {
+    const int ntiles = a.g.tiles_x * a.g.tiles_y;
+    if (!link)
+        k_merge<NW, HS><<<ntiles, kThreads, 0, s>>>(a, local_only ? 1 : 0, err);
+    else
+        k_link<NW, HS><<<ntiles, kThreads, 0, s>>>(a, err);
+}
+
+static void launch_tile_kernel(const ImageArgs &a, bool local_only, int *err, cudaStream_t s,
+                               bool link) {
+    const int nw = a.g.nw, hs = a.g.hs;
+#define CCL_CASE(NW_, HS_) \
+    if (nw == NW_ && hs == HS_) { launch_merge_link<NW_, HS_>(a, local_only, err, s, link); return; }
+    CCL_CASE(1, 1) CCL_CASE(2, 1) CCL_CASE(4, 1) CCL_CASE(8, 1)
+    CCL_CASE(1, 2) CCL_CASE(2, 2) CCL_CASE(4, 2) CCL_CASE(8, 2)
+#undef CCL_CASE
+}
+
+// Size-class table.  Tiles are 8192 (4-conn) or 16384 (8-conn) pixels; the
+// widest tile that does not exceed the next power of two >= W keeps idle
+// columns low and vertical seams rare.
+int default_tile_width(int height, int width, int conn) {
+    (void)height;
+    (void)conn;
+    if (width <= 32) return 32;
+    if (width <= 64) return 64;
+    if (width <= 128) return 128;
+    return 256;
+}
+
+// per host thread: events for the next enqueue_label call (benchmark hook)
+static thread_local cudaEvent_t t_phase_events[4];
+static thread_local bool t_phase_armed = false;
+
+ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, int width,
+                         int conn, int tile_w, unsigned flags, void *d_ws, size_t ws_bytes,
+                         cudaStream_t stream) {
+    if (!d_img || !d_labels || !valid_image_dims(height, width) || !valid_conn(conn))
+        return CCL_ERR_INVALID_ARG;
+    if (tile_w == 0) tile_w = default_tile_width(height, width, conn);
+    if (!valid_tile_w(tile_w)) return CCL_ERR_INVALID_ARG;
+    if (flags & ~(unsigned)CCL_FLAG_LOCAL_ONLY) return CCL_ERR_INVALID_ARG;
+    const Geom g = make_geom(height, width, conn, tile_w);
+    const size_t need = bits_bytes(g) + tiles_bytes(g);
+    ccl_status st = CCL_OK;
+    if (!d_ws) {
+        d_ws = library_workspace(stream, need, &st);
+        if (st != CCL_OK) return st;
+    } else if (ws_bytes < need || (reinterpret_cast<uintptr_t>(d_ws) & 255u)) {
+        return CCL_ERR_INVALID_ARG;
+    }
+    int *err = device_error_word();
+    if (!err) return CCL_ERR_CUDA;
+    ImageArgs a;
+    a.img = d_img;
+    a.labels = d_labels;
+    a.bits = static_cast<uint32_t *>(d_ws);
+    a.tws = reinterpret_cast<int *>(static_cast<char *>(d_ws) + bits_bytes(g));
+    a.g = g;
+    a.aligned16 = (width % 16 == 0) && (reinterpret_cast<uintptr_t>(d_img) % 16 == 0);
+    a.out_aligned16 = (width % 4 == 0) && (reinterpret_cast<uintptr_t>(d_labels) % 16 == 0);
+    const bool local_only = (flags & CCL_FLAG_LOCAL_ONLY) != 0;
+
+    const bool timed = t_phase_armed;
+    t_phase_armed = false;
+    if (timed) cudaEventRecord(t_phase_events[0], stream);
+    launch_tile_kernel(a, local_only, err, stream, false);
+    if (timed) cudaEventRecord(t_phase_events[1], stream);
+    const long long items = seam_items(g);
+    if (!local_only && items > 0) {
+        const long long blocks = (items + 255) / 256;
+        k_seams<<<(unsigned)blocks, 256, 0, stream>>>(a, items, err);
+    }
+    if (timed) cudaEventRecord(t_phase_events[2], stream);
+    launch_tile_kernel(a, local_only, err, stream, true);
+    if (timed) cudaEventRecord(t_phase_events[3], stream);
+    if (cudaGetLastError() != cudaSuccess) return CCL_ERR_CUDA;
+    return CCL_OK;
+}
+
+}  // namespace ccl
+
+extern "C" int ccl_default_tile_width(int height, int width, int connectivity) {
+    if (!ccl::valid_image_dims(height, width) || !ccl::valid_conn(connectivity)) return 0;
+    return ccl::default_tile_width(height, width, connectivity);
+}
+
+extern "C" size_t ccl_workspace_bytes_tiled(int height, int width, int connectivity,
+                                            int tile_w) {
+    if (!ccl::valid_image_dims(height, width) || !ccl::valid_conn(connectivity)) return 0;
+    if (tile_w == 0) tile_w = ccl::default_tile_width(height, width, connectivity);
+    if (!ccl::valid_tile_w(tile_w)) return 0;
+    const ccl::Geom g = ccl::make_geom(height, width, connectivity, tile_w);
+    return ccl::bits_bytes(g) + ccl::tiles_bytes(g);
+}
+
+extern "C" size_t ccl_workspace_bytes(int height, int width, int connectivity) {
+    return ccl_workspace_bytes_tiled(height, width, connectivity, 0);
+}
+
+extern "C" ccl_status ccl_label(const uint8_t *d_img, int32_t *d_labels, int height, int width,
+                                int connectivity, void *d_ws, size_t ws_bytes,
+                                ccl_stream stream) {
+    return ccl::enqueue_label(d_img, d_labels, height, width, connectivity, 0, 0u, d_ws,
+                              ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" ccl_status ccl_label_tiled(const uint8_t *d_img, int32_t *d_labels, int height,
+                                      int width, int connectivity, int tile_w, unsigned flags,
+                                      void *d_ws, size_t ws_bytes, ccl_stream stream) {
+    return ccl::enqueue_label(d_img, d_labels, height, width, connectivity, tile_w, flags, d_ws,
+                              ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" void ccl_set_phase_events(void *const *events) {
+    if (!events) { ccl::t_phase_armed = false; return; }
+    for (int k = 0; k < 4; ++k) ccl::t_phase_events[k] = static_cast<cudaEvent_t>(events[k]);
+    ccl::t_phase_armed = true;
+}

@@ -1,0 +1,413 @@
+// ccl_tile.cuh -- per-tile device routines shared by the single-image and
+// batched kernels: local merge (Kernel 1, §II-A), seam unions (Kernel 2,
+// §II-B) and link (§II-C).
+#pragma once
+
+#include "ccl_core.cuh"
+
+namespace ccl {
+
+// One image as the kernels see it.
+struct ImageArgs {
+    const uint8_t *img;
+    int32_t *labels;       // output, also the global union-find array
+    uint32_t *bits;        // bit image: H rows x nwg words
+    int *tws;              // per-tile workspace, g.tile_ints ints per tile
+    Geom g;
+    int aligned16;         // image rows start on 16-byte boundaries (W % 16 == 0)
+    int out_aligned16;     // label rows start on 16-byte boundaries (W % 4 == 0)
+};
+
+// Shared memory of the local-merge phase.
+struct SmemMerge {
+    int P[kNodeCap];          // parent of each segment node
+    int K[kNodeCap];          // tile-local key (min pixel index) | flags
+    uint32_t top[kThreads];   // first row of the strip, per word
+    uint32_t bot[kThreads];   // last row of the strip, per word
+    uint32_t st[kThreads];    // segment starts, per word
+    int base[kThreads];       // rank of the first segment starting in the word
+    int warp_sums[kThreads / 32];
+    int nborder;
+};
+
+// Shared memory of the link phase.
+struct SmemLink {
+    int S[kNodeCap];          // label per segment node
+    int R[kBorderCapMax];        // resolved label per border root
+    int warp_sums[kThreads / 32];
+};
+
+// rank of the segment containing column bit x (x in [-1, 31]) of a word with
+// segment starts `st` whose first start has rank `base`
+__device__ __forceinline__ int seg_rank(int base, uint32_t st, int x) {
+    return base + __popc(st & le_mask(x)) - 1;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 1 body: local merge of tile `tile` (§II-A).
+//
+// Thread (s, w) = (threadIdx.x / NW, threadIdx.x % NW) owns word w of strip s.
+// Output in the tile workspace:
+//   labels[n]  for every segment node n (rank order): 1 + global root index
+//              when the component stays inside the tile, else -(1 + j) with j
+//              the slot of its root in the border-root list;
+//   border[j]  global raster index of each root whose component reaches a
+//              seam with a neighbouring tile (also initialised as a root in the
+//              global union-find array G = labels buffer);
+//   records    global root index per seam pixel column/strip (-1: empty).
+template <int NW, int HS>
+__device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool local_only,
+                                           SmemMerge &sm, int *err) {
+    constexpr int NS = kThreads / NW;
+    constexpr int TW = 32 * NW;
+    constexpr int TH = NS * HS;
+    const Geom &g = a.g;
+    const int tid = threadIdx.x;
+    const int s = tid / NW, w = tid % NW;
+    const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const int gx = x0 + 32 * w;
+    const uint8_t *img_end = a.img + (size_t)g.H * (size_t)g.W;
+
+    // ---- a-1: stage the tile's pixels as bits (nonzero byte = foreground) ----
+    uint32_t rows[HS];
+#pragma unroll
+    for (int j = 0; j < HS; ++j) {
+        const int y = y0 + s * HS + j;
+        rows[j] = (y < g.H && gx < g.W)
+                      ? load_row_bits(a.img, img_end, y, gx, g.W, a.aligned16 != 0)
+                      : 0u;
+        if (y < g.H && (x0 / 32 + w) < g.nwg)
+            a.bits[(size_t)y * g.nwg + (x0 / 32 + w)] = rows[j];
+    }
+    const uint32_t top = rows[0], bot = rows[HS - 1];
+    const uint32_t m = top | bot;
+    uint32_t mL = __shfl_up_sync(0xFFFFFFFFu, m, 1);
+    mL = (w > 0) ? (mL >> 31) : 0u;
+    const uint32_t st = m & ~((m << 1) | mL);
+    int total;
+    const int base = block_excl_scan(__popc(st), sm.warp_sums, total);
+    sm.top[tid] = top;
+    sm.bot[tid] = bot;
+    sm.st[tid] = st;
+    sm.base[tid] = base;
+
+    // ---- nodes: parent = self, key = smallest tile-local pixel index ----
+    {
+        uint32_t rem = st;
+        int n = base;
+        while (rem) {
+            const int i = __ffs(rem) - 1;
+            rem &= rem - 1;
+            int key;
+            if (HS == 2) {
+                // length of the run from bit i to the end of this word (<= 32 - i)
+                const int len = __ffsll(~((unsigned long long)m >> i)) - 1;
+                const uint32_t part = (uint32_t)(((1ull << len) - 1ull) << i);
+                const uint32_t tp = top & part;
+                key = tp ? ((2 * s) * TW + 32 * w + (__ffs(tp) - 1))
+                         : ((2 * s + 1) * TW + 32 * w + i);
+            } else {
+                key = s * TW + 32 * w + i;
+            }
+            sm.P[n] = n;
+            sm.K[n] = key;
+            ++n;
+        }
+    }
+    if (tid == 0) sm.nborder = 0;
+    __syncthreads();
+    if (HS == 2 && (m & 1u) && !(st & 1u)) {
+        // this word continues a segment started in an earlier word; a top-row
+        // pixel here may be the segment's smallest index
+        const int len = __ffsll(~(unsigned long long)m) - 1;
+        const uint32_t part = (uint32_t)((1ull << len) - 1ull);
+        const uint32_t tp = top & part;
+        if (tp) atomicMin(&sm.K[base - 1], (2 * s) * TW + 32 * w + (__ffs(tp) - 1));
+    }
+    __syncthreads();
+
+    // ---- a-2: unions between strip s-1 and strip s, one per touching run pair ----
+    if (s > 0) {
+        const int up = tid - NW;
+        const uint32_t av = sm.bot[up];
+        const uint32_t bv = sm.top[tid];
+        const uint32_t aL = w > 0 ? (sm.bot[up - 1] >> 31) : 0u;
+        const uint32_t bL = w > 0 ? (sm.top[tid - 1] >> 31) : 0u;
+        const int baseA = sm.base[up];
+        const uint32_t stA = sm.st[up];
+        const uint32_t o = av & bv;
+        const uint32_t os = o & ~((o << 1) | (aL & bL));
+        int la = -1, lb = -1;
+        uint32_t rem = os;
+        while (rem) {
+            const int x = __ffs(rem) - 1;
+            rem &= rem - 1;
+            const int ra = seg_rank(baseA, stA, x), rb = seg_rank(base, st, x);
+            if (ra != la || rb != lb) { sunion(sm.P, sm.K, ra, rb, err); la = ra; lb = rb; }
+        }
+        if (HS == 2) {
+            const uint32_t aR = w < NW - 1 ? (sm.bot[up + 1] & 1u) : 0u;
+            const uint32_t bR = w < NW - 1 ? (sm.top[tid + 1] & 1u) : 0u;
+            const uint32_t stA_next0 = w < NW - 1 ? (sm.st[up + 1] & 1u) : 0u;
+            // b-run starts at x right after an a-run that ends at x-1
+            uint32_t dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
+            // b-run ends at x right before an a-run that starts at x+1
+            uint32_t dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31));
+            while (dr) {
+                const int x = __ffs(dr) - 1;
+                dr &= dr - 1;
+                const int ra = seg_rank(baseA, stA, x - 1), rb = seg_rank(base, st, x);
+                if (ra != la || rb != lb) { sunion(sm.P, sm.K, ra, rb, err); la = ra; lb = rb; }
+            }
+            while (dl) {
+                const int x = __ffs(dl) - 1;
+                dl &= dl - 1;
+                const int ra = (x == 31) ? (baseA + __popc(stA) + (int)stA_next0 - 1)
+                                         : seg_rank(baseA, stA, x + 1);
+                const int rb = seg_rank(base, st, x);
+                if (ra != la || rb != lb) { sunion(sm.P, sm.K, ra, rb, err); la = ra; lb = rb; }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- roots: compress every node to its root ----
+    for (int n = tid; n < total; n += kThreads) sm.P[n] = sfind(sm.P, n, err);
+    __syncthreads();
+
+    int *tw_ = a.tws + (size_t)tile * g.tile_ints;
+    int *rec = tw_ + g.off_rec;
+    auto gkey = [&](int k) -> int {
+        const int ly = k >> g.log2tw, lx = k & (TW - 1);
+        return (y0 + ly) * g.W + x0 + lx;
+    };
+    const bool has_up = ty > 0, has_down = ty < g.tiles_y - 1;
+    const bool has_left = tx > 0, has_right = tx < g.tiles_x - 1;
+
+    // ---- seam records (top/bottom per column, left/right per strip) and flags ----
+    if (tid < TW) {
+        const int wc = tid >> 5, b = tid & 31;
+        {   // top: strip 0
+            const int o = wc;
+            const bool on = (sm.top[o] | sm.bot[o]) >> b & 1u;
+            int v = -1;
+            if (on) {
+                const int r = sm.P[seg_rank(sm.base[o], sm.st[o], b)];
+                v = gkey(sm.K[r] & kKeyMask);
+                if (has_up && !local_only && ((sm.top[o] >> b) & 1u)) atomicOr(&sm.K[r], kKeyFlag);
+            }
+            rec[tid] = v;
+        }
+        {   // bottom: strip NS-1
+            const int o = (NS - 1) * NW + wc;
+            const bool on = (sm.top[o] | sm.bot[o]) >> b & 1u;
+            int v = -1;
+            if (on) {
+                const int r = sm.P[seg_rank(sm.base[o], sm.st[o], b)];
+                v = gkey(sm.K[r] & kKeyMask);
+                if (has_down && !local_only && ((sm.bot[o] >> b) & 1u)) atomicOr(&sm.K[r], kKeyFlag);
+            }
+            rec[TW + tid] = v;
+        }
+    }
+    if (tid < NS) {
+        {   // left: column 0 of strip tid (always a segment start when set)
+            const int o = tid * NW;
+            int v = -1;
+            if ((sm.top[o] | sm.bot[o]) & 1u) {
+                const int r = sm.P[sm.base[o]];
+                v = gkey(sm.K[r] & kKeyMask);
+                if (has_left && !local_only) atomicOr(&sm.K[r], kKeyFlag);
+            }
+            rec[2 * TW + tid] = v;
+        }
+        {   // right: column TW-1 of strip tid
+            const int o = tid * NW + NW - 1;
+            int v = -1;
+            if ((sm.top[o] | sm.bot[o]) >> 31) {
+                const int r = sm.P[seg_rank(sm.base[o], sm.st[o], 31)];
+                v = gkey(sm.K[r] & kKeyMask);
+                if (has_right && !local_only) atomicOr(&sm.K[r], kKeyFlag);
+            }
+            rec[2 * TW + NS + tid] = v;
+        }
+    }
+    __syncthreads();
+
+    // ---- border roots: list slot + global union-find root entry ----
+    if (!local_only) {
+        for (int n = tid; n < total; n += kThreads) {
+            const int k = sm.K[n];
+            if (sm.P[n] == n && (k & kKeyFlag)) {
+                const int j = atomicAdd(&sm.nborder, 1);
+                if (j < g.border_cap) {
+                    const int gk = gkey(k & kKeyMask);
+                    tw_[g.off_border + j] = gk;
+                    a.labels[gk] = (int)((uint32_t)gk | kEncBit);
+                    sm.K[n] = kKeyFlag | j;
+                } else {
+                    atomicOr(err, kErrBorderCap);
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- per-segment labels ----
+    for (int n = tid; n < total; n += kThreads) {
+        const int k = sm.K[sm.P[n]];
+        tw_[kHdrInts + n] = (k & kKeyFlag) ? -(1 + (k & kKeyMask)) : 1 + gkey(k & kKeyMask);
+    }
+    if (tid == 0) tw_[0] = local_only ? 0 : min(sm.nborder, g.border_cap);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 2 body: seam unions (§II-B).  Work item `idx` in
+// [0, (tiles_y-1)*nwg) is one word of a horizontal seam (rows y-1, y with
+// y = ty*TH); the rest, (tiles_x-1)*tiles_y*NS items, are one strip of a
+// vertical seam.  Each touching pair of runs across the seam is unioned once.
+__device__ __forceinline__ uint32_t bit_at(const uint32_t *bits, int nwg, int y, int x) {
+    return (__ldcg(bits + (size_t)y * nwg + (x >> 5)) >> (x & 31)) & 1u;
+}
+
+__device__ __forceinline__ void seam_item(const ImageArgs &a, long long idx, int *err) {
+    const Geom &g = a.g;
+    const long long nh = (long long)(g.tiles_y - 1) * g.nwg;
+    int *G = a.labels;
+    if (idx < nh) {
+        const int ty = (int)(idx / g.nwg) + 1;
+        const int j = (int)(idx % g.nwg);
+        const int y = ty * g.th;
+        const uint32_t *ra_ = a.bits + (size_t)(y - 1) * g.nwg;
+        const uint32_t *rb_ = a.bits + (size_t)y * g.nwg;
+        const uint32_t av = __ldcg(ra_ + j), bv = __ldcg(rb_ + j);
+        if (!bv) return;   // every contact needs a pixel in row y
+        const uint32_t aL = j > 0 ? (__ldcg(ra_ + j - 1) >> 31) : 0u;
+        const uint32_t bL = j > 0 ? (__ldcg(rb_ + j - 1) >> 31) : 0u;
+        const uint32_t aR = j < g.nwg - 1 ? (__ldcg(ra_ + j + 1) & 1u) : 0u;
+        const uint32_t bR = j < g.nwg - 1 ? (__ldcg(rb_ + j + 1) & 1u) : 0u;
+        const int *tbase_up = a.tws + (size_t)(ty - 1) * g.tiles_x * g.tile_ints + g.off_rec + g.tw;
+        const int *tbase_dn = a.tws + (size_t)ty * g.tiles_x * g.tile_ints + g.off_rec;
+        auto rec_up = [&](int xg) { return __ldcg(tbase_up + (size_t)(xg >> g.log2tw) * g.tile_ints + (xg & (g.tw - 1))); };
+        auto rec_dn = [&](int xg) { return __ldcg(tbase_dn + (size_t)(xg >> g.log2tw) * g.tile_ints + (xg & (g.tw - 1))); };
+        int la = -1, lb = -1;
+        auto contact = [&](int xa, int xb) {
+            const int ka = rec_up(xa), kb = rec_dn(xb);
+            if (ka != la || kb != lb) { gunion(G, ka, kb, err); la = ka; lb = kb; }
+        };
+        const uint32_t o = av & bv;
+        uint32_t os = o & ~((o << 1) | (aL & bL));
+        const int xw = 32 * j;
+        while (os) { const int x = __ffs(os) - 1; os &= os - 1; contact(xw + x, xw + x); }
+        if (g.hs == 2) {
+            uint32_t dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
+            uint32_t dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31));
+            while (dr) { const int x = __ffs(dr) - 1; dr &= dr - 1; contact(xw + x - 1, xw + x); }
+            while (dl) { const int x = __ffs(dl) - 1; dl &= dl - 1; contact(xw + x + 1, xw + x); }
+        }
+        return;
+    }
+    idx -= nh;
+    const int s = (int)(idx % g.ns);
+    const long long t = idx / g.ns;
+    const int ty = (int)(t % g.tiles_y);
+    const int tx = (int)(t / g.tiles_y) + 1;
+    const int x = tx * g.tw;
+    const int r0 = ty * g.th + s * g.hs;
+    if (r0 >= g.H) return;
+    const int *recL = a.tws + ((size_t)ty * g.tiles_x + (tx - 1)) * g.tile_ints + g.off_rec + 2 * g.tw + g.ns;
+    const int *recR = a.tws + ((size_t)ty * g.tiles_x + tx) * g.tile_ints + g.off_rec + 2 * g.tw;
+    const uint32_t l0 = bit_at(a.bits, g.nwg, r0, x - 1), r0b = bit_at(a.bits, g.nwg, r0, x);
+    uint32_t l1 = 0, r1b = 0;
+    if (g.hs == 2 && r0 + 1 < g.H) {
+        l1 = bit_at(a.bits, g.nwg, r0 + 1, x - 1);
+        r1b = bit_at(a.bits, g.nwg, r0 + 1, x);
+    }
+    if ((l0 | l1) && (r0b | r1b)) gunion(G, __ldcg(recL + s), __ldcg(recR + s), err);
+    if (g.hs == 2 && s > 0) {
+        // diagonals between the last row of strip s-1 and the first of strip s
+        const uint32_t lu = bit_at(a.bits, g.nwg, r0 - 1, x - 1);
+        const uint32_t ru = bit_at(a.bits, g.nwg, r0 - 1, x);
+        if (lu && r0b) gunion(G, __ldcg(recL + s - 1), __ldcg(recR + s), err);
+        if (l0 && ru) gunion(G, __ldcg(recL + s), __ldcg(recR + s - 1), err);
+    }
+}
+
+__host__ __device__ inline long long seam_items(const Geom &g) {
+    return (long long)(g.tiles_y - 1) * g.nwg + (long long)(g.tiles_x - 1) * g.tiles_y * g.ns;
+}
+
+// ---------------------------------------------------------------------------
+// Link body (§II-C): re-derive the segments of the tile from the bit image,
+// resolve the border roots through the global array, write one int32 label
+// per pixel.
+template <int NW, int HS>
+__device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink &sm, int *err) {
+    constexpr int NS = kThreads / NW;
+    constexpr int TW = 32 * NW;
+    constexpr int TH = NS * HS;
+    const Geom &g = a.g;
+    const int tid = threadIdx.x;
+    const int s = tid / NW, w = tid % NW;
+    const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const int gwi = x0 / 32 + w;
+    const int gx = x0 + 32 * w;
+
+    uint32_t rows[HS];
+#pragma unroll
+    for (int j = 0; j < HS; ++j) {
+        const int y = y0 + s * HS + j;
+        rows[j] = (y < g.H && gwi < g.nwg) ? __ldcg(a.bits + (size_t)y * g.nwg + gwi) : 0u;
+    }
+    const uint32_t m = rows[0] | rows[HS - 1];
+    uint32_t mL = __shfl_up_sync(0xFFFFFFFFu, m, 1);
+    mL = (w > 0) ? (mL >> 31) : 0u;
+    const uint32_t st = m & ~((m << 1) | mL);
+    int total;
+    const int base = block_excl_scan(__popc(st), sm.warp_sums, total);
+
+    const int *tw_ = a.tws + (size_t)tile * g.tile_ints;
+    for (int n = tid; n < total; n += kThreads) sm.S[n] = __ldcg(tw_ + kHdrInts + n);
+    const int nb = __ldcg(tw_);
+    for (int j = tid; j < nb; j += kThreads) sm.R[j] = gresolve(a.labels, __ldcg(tw_ + g.off_border + j), err);
+    __syncthreads();
+    for (int n = tid; n < total; n += kThreads) {
+        const int v = sm.S[n];
+        if (v < 0) sm.S[n] = sm.R[-v - 1];
+    }
+    __syncthreads();
+
+    if (gx >= g.W) return;
+    const int ncol = min(32, g.W - gx);
+#pragma unroll
+    for (int j = 0; j < HS; ++j) {
+        const int y = y0 + s * HS + j;
+        if (y >= g.H) break;
+        const uint32_t rb = rows[j];
+        int32_t *out = a.labels + (size_t)y * g.W + gx;
+        if (a.out_aligned16 && ncol == 32) {
+            int cur = base - 1;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                int v[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = 4 * q + e;
+                    cur += (st >> c) & 1u;
+                    v[e] = ((rb >> c) & 1u) ? sm.S[cur < 0 ? 0 : cur] : 0;
+                }
+                __stcs(reinterpret_cast<int4 *>(out) + q, make_int4(v[0], v[1], v[2], v[3]));
+            }
+        } else {
+            int cur = base - 1;
+            for (int c = 0; c < ncol; ++c) {
+                cur += (st >> c) & 1u;
+                out[c] = ((rb >> c) & 1u) ? sm.S[cur < 0 ? 0 : cur] : 0;
+            }
+        }
+    }
+}
+
+}  // namespace ccl

@@ -1,0 +1,199 @@
+"""Single-image GPU path vs the CPU oracle: bit-exact on every seeded input.
+
+Covers every tile width, both connectivities, ragged tails and partial tiles,
+unaligned image/label pointers, exhaustive tiny images, structured extremes,
+the local-merge-only output, repeat runs, and the full-size headline config.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1708_08180_gb300 as ccl  # noqa: E402
+
+DEV = "cuda:0"
+TILES = [32, 64, 128, 256]
+
+
+def gpu_label(img, conn, tile_w=0, flags=0, img_offset=0, out_offset=0):
+    """Run the library on a copy of `img` placed `img_offset` bytes into a
+    device buffer (to exercise unaligned rows) and return the labels."""
+    h, w = img.shape
+    buf = torch.empty(h * w + 64, dtype=torch.uint8, device=DEV)
+    dimg = buf[img_offset:img_offset + h * w].view(h, w)
+    dimg.copy_(torch.from_numpy(np.ascontiguousarray(img)))
+    obuf = torch.empty(h * w + 16, dtype=torch.int32, device=DEV)
+    out = obuf[out_offset:out_offset + h * w].view(h, w)
+    ccl.ccl_label_tiled(dimg, conn, tile_w, flags, out=out)
+    ccl.ccl_sync()
+    return out.cpu().numpy()
+
+
+def assert_same(got, want, what=""):
+    if not np.array_equal(got, want):
+        bad = np.argwhere(got != want)
+        y, x = bad[0]
+        raise AssertionError(f"{what}: {len(bad)} labels differ; first at y={y} x={x}: "
+                             f"got {got[y, x]} want {want[y, x]}")
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("tile_w", TILES)
+def test_random_sizes_all_tiles(conn, tile_w):
+    rng = np.random.default_rng(1000 + tile_w + conn)
+    th = (256 // (tile_w // 32)) * (2 if conn == 8 else 1)
+    for k in range(6):
+        h = int(rng.integers(1, 3 * th + 7))
+        w = int(rng.integers(1, 4 * tile_w + 45))
+        p = [0.1, 0.3, 0.45, 0.5, 0.6, 0.9][k]
+        img = synthetic.bernoulli(h, w, p, k, cfg_id=20)
+        assert_same(gpu_label(img, conn, tile_w), oracle.label(img, conn), f"{h}x{w} p={p}")
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("hw", [(1, 1), (1, 2), (2, 1), (1, 1000), (1000, 1), (33, 17), (3, 4097),
+                                (4099, 3), (517, 300), (1080, 1920), (640, 2049)])
+def test_edge_shapes(hw, conn):
+    h, w = hw
+    for p in (0.5, 0.95):
+        img = synthetic.bernoulli(h, w, p, 1, cfg_id=21)
+        assert_same(gpu_label(img, conn), oracle.label(img, conn), f"{h}x{w} p={p}")
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_unaligned_pointers(conn):
+    img = synthetic.bernoulli(77, 301, 0.55, 2, cfg_id=22)
+    want = oracle.label(img, conn)
+    for off in (1, 2, 3, 5, 13):
+        assert_same(gpu_label(img, conn, 0, 0, img_offset=off, out_offset=off % 4), want,
+                    f"offset {off}")
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_exhaustive_tiny_images(conn):
+    """Every binary image up to 4x4 (74,954), each through the plain path:
+    packed back to back in one device buffer (unaligned starts)."""
+    from helpers import all_images
+
+    for h in range(1, 5):
+        for w in range(1, 5):
+            imgs = all_images(h, w)
+            want = oracle.label_many(imgs, conn)
+            n = imgs.shape[0]
+            dimg = torch.from_numpy(imgs.reshape(-1)).to(DEV)
+            dout = torch.empty(n * h * w, dtype=torch.int32, device=DEV)
+            ws = torch.empty(ccl.ccl_workspace_bytes(h, w, conn), dtype=torch.uint8, device=DEV)
+            for k in range(n):
+                ccl.ccl_label(dimg[k * h * w:(k + 1) * h * w].view(h, w), conn,
+                              out=dout[k * h * w:(k + 1) * h * w].view(h, w), ws=ws)
+            ccl.ccl_sync()
+            got = dout.view(n, h, w).cpu().numpy()
+            bad = np.nonzero(np.any(got != want, axis=(1, 2)))[0]
+            assert bad.size == 0, f"{h}x{w}: images {bad[:5]} differ"
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("tile_w", TILES)
+def test_structured(conn, tile_w):
+    h = w = 1024
+    cases = [(n, im) for n, im in synthetic.structured_set(h, w)]
+    cases.append(("checker", synthetic.checkerboard(h, w)))
+    for name, img in cases:
+        assert_same(gpu_label(img, conn, tile_w), oracle.label(img, conn), name)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("tile_w", TILES)
+def test_local_merge_only_matches_per_tile_oracle(conn, tile_w):
+    th = (256 // (tile_w // 32)) * (2 if conn == 8 else 1)
+    img = synthetic.bernoulli(2 * th + 19, 3 * tile_w + 11, 0.5, 3, cfg_id=23)
+    want = oracle.label_tiles(img, conn, tile_w, th)
+    assert_same(gpu_label(img, conn, tile_w, ccl.CCL_FLAG_LOCAL_ONLY), want, "local-only")
+
+
+def test_foreground_byte_value_irrelevant():
+    img = synthetic.bernoulli(300, 333, 0.5, 4, cfg_id=24)
+    for conn in (4, 8):
+        a = gpu_label(img, conn)
+        assert_same(gpu_label(img * 255, conn), a, "255")
+        assert_same(gpu_label(img * 7, conn), a, "7")
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_repeat_runs_identical(conn):
+    """Union order varies run to run; the canonical result may not."""
+    img = synthetic.bernoulli(2048, 2048, 0.6 if conn == 4 else 0.45, 5, cfg_id=25)
+    want = oracle.label(img, conn)
+    dimg = torch.from_numpy(img).to(DEV)
+    out = torch.empty((2048, 2048), dtype=torch.int32, device=DEV)
+    ws = torch.empty(ccl.ccl_workspace_bytes(2048, 2048, conn), dtype=torch.uint8, device=DEV)
+    for _ in range(20):
+        out.fill_(-5)
+        ccl.ccl_label(dimg, conn, out=out, ws=ws)
+        ccl.ccl_sync()
+        assert_same(out.cpu().numpy(), want, "repeat")
+
+
+@pytest.mark.parametrize("p", [0.1, 0.4, 0.5, 0.6, 0.9])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_density_sweep_4096(p, conn):
+    img = synthetic.bernoulli(4096, 4096, p, 0)
+    assert_same(gpu_label(img, conn), oracle.label(img, conn), f"4096 p={p}")
+
+
+def test_full_size_headline_8192():
+    """The benchmark's workload (8192^2, p = 0.5, 8-connectivity, default tile)
+    compared in full with the oracle, in the launch configuration bench.py
+    times (ccl_label with a caller workspace on the current stream)."""
+    img = synthetic.bernoulli(8192, 8192, 0.5, 0)
+    want = oracle.label(img, 8)
+    dimg = torch.from_numpy(img).to(DEV)
+    ws = torch.empty(ccl.ccl_workspace_bytes(8192, 8192, 8), dtype=torch.uint8, device=DEV)
+    out = ccl.ccl_label(dimg, 8, ws=ws)
+    ccl.ccl_sync()
+    assert_same(out.cpu().numpy(), want, "8192 headline")
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_structured_4096(conn):
+    for name, img in synthetic.structured_set(4096, 4096):
+        assert_same(gpu_label(img, conn), oracle.label(img, conn), name)
+
+
+def test_ring_closed_form_on_gpu():
+    h = w = 4096
+    img = synthetic.rings(h, w)
+    for conn in (4, 8):
+        got = gpu_label(img, conn)
+        for d in synthetic.ring_insets(h, w):
+            assert got[d, d] == 1 + d * w + d
+            assert got[h - 1 - d, w - 1 - d] == 1 + d * w + d
+
+
+def test_invalid_args_enqueue_nothing():
+    img = torch.zeros((8, 8), dtype=torch.uint8, device=DEV)
+    with pytest.raises(ccl.CclError):
+        ccl.ccl_label_tiled(img, 6)
+    with pytest.raises(ccl.CclError):
+        ccl.ccl_label_tiled(img, 8, tile_w=48)
+    small = torch.empty(16, dtype=torch.uint8, device=DEV)
+    with pytest.raises(ccl.CclError):
+        ccl.ccl_label(img, 8, ws=small)
+    ccl.ccl_sync()
+
+
+def test_library_workspace_when_none_given():
+    from paper_1708_08180_gb300 import _lib
+
+    img = synthetic.bernoulli(300, 500, 0.5, 6, cfg_id=26)
+    dimg = torch.from_numpy(img).to(DEV)
+    out = torch.empty((300, 500), dtype=torch.int32, device=DEV)
+    st = _lib.load().ccl_label(dimg.data_ptr(), out.data_ptr(), 300, 500, 8, None, 0,
+                               torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    ccl.ccl_sync()
+    assert_same(out.cpu().numpy(), oracle.label(img, 8), "library workspace")
