@@ -208,6 +208,18 @@ __device__ __forceinline__ int sfind(volatile int *P, int x, int *err) {
     return x;
 }
 
+// Read-only find, for the pass that stores every node's root: with no
+// path-halving stores, each P[n] ends the pass holding exactly its root.
+__device__ __forceinline__ int sfind_ro(volatile const int *P, int x, int *err) {
+    for (int it = 0; it < kSmemLoopCap; ++it) {
+        const int p = P[x];
+        if (p == x) return x;
+        x = p;
+    }
+    atomicOr(err, kErrSmemFind);
+    return x;
+}
+
 __device__ __forceinline__ void sunion(int *P, const int *K, int a, int b, int *err) {
     volatile int *vP = P;
     volatile const int *vK = K;

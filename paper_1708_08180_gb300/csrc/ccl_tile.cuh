@@ -172,8 +172,10 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     }
     __syncthreads();
 
-    // ---- roots: compress every node to its root ----
-    for (int n = tid; n < total; n += kThreads) sm.P[n] = sfind(sm.P, n, err);
+    // ---- roots: every node points straight at its root ----
+    // Read-only finds: a path-halving store by one thread could otherwise land
+    // after another thread's root store and leave a non-root parent behind.
+    for (int n = tid; n < total; n += kThreads) sm.P[n] = sfind_ro(sm.P, n, err);
     __syncthreads();
 
     int *tw_ = a.tws + (size_t)tile * g.tile_ints;
@@ -370,12 +372,20 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
 
     const int *tw_ = a.tws + (size_t)tile * g.tile_ints;
     for (int n = tid; n < total; n += kThreads) sm.S[n] = __ldcg(tw_ + kHdrInts + n);
-    const int nb = __ldcg(tw_);
+    const int nb = min(__ldcg(tw_), kBorderCapMax);
     for (int j = tid; j < nb; j += kThreads) sm.R[j] = gresolve(a.labels, __ldcg(tw_ + g.off_border + j), err);
     __syncthreads();
     for (int n = tid; n < total; n += kThreads) {
         const int v = sm.S[n];
-        if (v < 0) sm.S[n] = sm.R[-v - 1];
+        if (v < 0) {
+            const int j = -v - 1;
+            if (j < nb) {
+                sm.S[n] = sm.R[j];
+            } else {
+                sm.S[n] = 0;
+                atomicOr(err, kErrBorderCap);
+            }
+        }
     }
     __syncthreads();
 
