@@ -195,7 +195,7 @@ def cpu_baseline(img, budget_s: float = 15.0):
         times.append(time.perf_counter() - t0)
     med = statistics.median(times)
     return {"value": img.size / med / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle BFS on the full {H}x{W} p={P} 8-conn image, {len(times)} runs, "
+            "sample": f"oracle BFS on the full {H}x{W} p={P} {CONN}-conn image, {len(times)} runs, "
                       f"median {med:.3f} s", "runs": len(times)}
 
 
@@ -226,13 +226,13 @@ def run_reference(args, rank, world):
     dt = time.perf_counter() - t0
     value = sample.size * args.steps / dt / 1e9
     desc = (f"oracle BFS (single thread) on the first {rows} rows ({rows}x{W}) of the "
-            f"{H}x{W} p={P} 8-conn benchmark image per step")
+            f"{H}x{W} p={P} {CONN}-conn benchmark image per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"{H}x{W} uint8 Bernoulli(p={P}), 8-connectivity, CPU oracle",
+        "config": {"workload": f"{H}x{W} uint8 Bernoulli(p={P}), {CONN}-connectivity, CPU oracle",
                    "sample_rows": rows},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": desc},
@@ -301,6 +301,9 @@ def run_ours(args, rank, world, local):
 
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    for e4 in ev:                      # materialise the CUDA events outside the timing
+        for e in e4:
+            e.record(stream)
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     props = torch.cuda.get_device_properties(dev)
@@ -362,8 +365,9 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"{H}x{W} uint8 Bernoulli(p={P}) image, 8-connectivity, plain "
-                               "single-image path (ccl_label), tile 256x64",
+        "config": {"workload": f"{H}x{W} uint8 Bernoulli(p={P}) image, {CONN}-connectivity, "
+                               "plain single-image path (ccl_label)",
+                   "tile": f"{ccl.ccl_default_tile_width(H, W, CONN)} px wide",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": f"{ROTATE} distinct inputs/outputs/workspaces rotated per step "
                          f"({ROTATE} x 320 MiB > 129 MB L2), no flush"},
@@ -392,7 +396,17 @@ def main(argv=None) -> int:
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=8192, help="image side (default 8192)")
+    ap.add_argument("--density", type=float, default=0.5, help="Bernoulli p (default 0.5)")
+    ap.add_argument("--conn", type=int, choices=(4, 8), default=8)
+    ap.add_argument("--rotate", type=int, default=3,
+                    help="distinct input/output/workspace sets cycled per step (default 3)")
     args = ap.parse_args(argv)
+    global H, W, P, CONN, ROTATE
+    H = W = args.size
+    P = args.density
+    CONN = args.conn
+    ROTATE = max(1, args.rotate)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, local = dist_env()

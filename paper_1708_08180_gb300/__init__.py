@@ -173,6 +173,9 @@ def ccl_set_phase_events(events) -> None:
     if events is None:
         load().ccl_set_phase_events(None)
         return
+    for e in events:
+        if not int(e.cuda_event):      # torch creates the CUDA event on first record
+            e.record()
     arr = (ctypes.c_void_p * 4)(*[int(e.cuda_event) for e in events])
     load().ccl_set_phase_events(arr)
 
