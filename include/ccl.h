@@ -129,6 +129,35 @@ ccl_status ccl_sync(ccl_stream stream);
 /* Free library-owned workspaces and batched-path state on every device. */
 ccl_status ccl_shutdown(void);
 
+/* Allocation-free variant of ccl_label (the paper has no counterpart; it
+ * exists for callers that cannot allocate device memory: code inside a host
+ * framework that owns every device allocation through its own allocator,
+ * plug-ins that are handed only input and output pointers, and latency-
+ * critical loops that cannot afford cudaMalloc's implicit device
+ * synchronisation or an allocation failure mid-stream).
+ *
+ * Same result, arguments, layout and ownership as ccl_label, but the scratch
+ * lives in a fixed device array of CCL_STATIC_SCRATCH_BYTES inside this
+ * library (held on every GPU that loads the library until the process
+ * exits); the caller passes only the image and the labels.  The call makes no
+ * cudaMalloc, cudaFree or other allocating call.
+ *   - Limit: ccl_workspace_bytes(height, width, connectivity) must not exceed
+ *     CCL_STATIC_SCRATCH_BYTES (this covers every image up to 4096 x 4096 at
+ *     either connectivity); larger images return CCL_ERR_INVALID_ARG and
+ *     nothing is enqueued.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture.
+ *   - All calls on a device share the one array and it keeps the previous
+ *     call's contents (nothing in it needs clearing: every word is written
+ *     before it is read).  Calls whose work overlaps on the GPU (different
+ *     streams, or different host threads) race on the array and corrupt each
+ *     other's results: serialise them, e.g. on one stream.
+ * Errors: CCL_ERR_INVALID_ARG (bad arguments or too large), CCL_ERR_CUDA. */
+#define CCL_STATIC_SCRATCH_BYTES (64u << 20)
+ccl_status ccl_label_static(const uint8_t *d_img, int32_t *d_labels, int height, int width,
+                            int connectivity, ccl_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batched: many images of different sizes in one launch sequence           */
 /* ------------------------------------------------------------------------ */

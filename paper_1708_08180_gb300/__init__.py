@@ -23,7 +23,8 @@ __all__ = [
     "CclError", "CCL_FLAG_LOCAL_ONLY", "label", "label_batched", "ccl_label", "ccl_label_tiled",
     "ccl_label_batched", "ccl_workspace_bytes", "ccl_workspace_bytes_tiled",
     "ccl_batched_workspace_bytes", "ccl_default_tile_width", "ccl_seam_pair_count", "ccl_sync",
-    "ccl_shutdown", "ccl_status_string", "ccl_set_phase_events", "Server", "load",
+    "ccl_shutdown", "ccl_status_string", "ccl_set_phase_events", "ccl_label_static", "Server",
+    "load",
 ]
 
 
@@ -114,6 +115,24 @@ def ccl_label(img, conn: int = 8, out=None, ws=None, stream=None):
         st = load().ccl_label(img.data_ptr(), out.data_ptr(), h, w, conn, ws.data_ptr(),
                               ws.numel(), _stream_handle(stream))
     check(st, "ccl_label")
+    return out
+
+
+def ccl_label_static(img, conn: int = 8, out=None, stream=None):
+    """Label one image without allocating device memory in the library: the
+    scratch is the library's fixed device array (see ``include/ccl.h``).  Only
+    ``out`` is allocated here when None; images whose workspace exceeds
+    ``CCL_STATIC_SCRATCH_BYTES`` raise.  Calls that overlap on the GPU race on
+    the shared scratch, so keep them on one stream."""
+    torch = _torch()
+    _check_img(img)
+    h, w = img.shape
+    if out is None:
+        out = torch.empty((h, w), dtype=torch.int32, device=img.device)
+    with torch.cuda.device(img.device):
+        st = load().ccl_label_static(img.data_ptr(), out.data_ptr(), h, w, conn,
+                                     _stream_handle(stream))
+    check(st, "ccl_label_static")
     return out
 
 

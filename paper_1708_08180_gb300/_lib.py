@@ -25,6 +25,7 @@ CCL_ERR_SHUTDOWN = 6
 CCL_ERR_NOT_FOUND = 7
 CCL_ERR_PENDING = 8
 CCL_FLAG_LOCAL_ONLY = 1
+CCL_STATIC_SCRATCH_BYTES = 64 << 20
 
 
 class CclError(RuntimeError):
@@ -55,6 +56,7 @@ _SIGS = {
     "ccl_label": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_int, _P, _c.c_size_t, _P]),
     "ccl_label_tiled": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint,
                                    _P, _c.c_size_t, _P]),
+    "ccl_label_static": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_int, _P]),
     "ccl_seam_pair_count": (_c.c_longlong, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int]),
     "ccl_sync": (_c.c_int, [_P]),
     "ccl_set_phase_events": (None, [_c.POINTER(_P)]),

@@ -31,4 +31,9 @@ int default_tile_width(int height, int width, int conn);
 // Release batched-path state.
 void free_batched_state();
 
+// Enqueue the three single-image kernels with the given workspace (ccl_plain.cu).
+ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, int width,
+                         int conn, int tile_w, unsigned flags, void *d_ws, size_t ws_bytes,
+                         cudaStream_t stream);
+
 }  // namespace ccl
