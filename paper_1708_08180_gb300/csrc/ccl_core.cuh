@@ -242,16 +242,22 @@ __device__ __forceinline__ void sunion(int *P, const int *K, int a, int b, int *
 __device__ __forceinline__ int gload(const int *p) { return __ldcg(p); }
 
 __device__ __forceinline__ int gfind(int *G, int x, int *err) {
-    for (int it = 0; it < kGlobLoopCap; ++it) {
-        int p = (int)((uint32_t)gload(G + x) & ~kEncBit);
-        if (p == x) return x;
-        int g = (int)((uint32_t)gload(G + p) & ~kEncBit);
-        if (g == p) return p;
-        __stcg(G + x, (int)((uint32_t)g | kEncBit));   // path halving
-        x = g;
+    // walk to the root, then point every node of the walked path at it
+    int r = x;
+    for (int it = 0;; ++it) {
+        const int p = (int)((uint32_t)gload(G + r) & ~kEncBit);
+        if (p == r) break;
+        if (it >= kGlobLoopCap) { atomicOr(err, kErrGlobFind); return r; }
+        r = p;
     }
-    atomicOr(err, kErrGlobFind);
-    return x;
+    const int er = (int)((uint32_t)r | kEncBit);
+    for (int it = 0; x != r && it < kGlobLoopCap; ++it) {
+        const int p = (int)((uint32_t)gload(G + x) & ~kEncBit);
+        if (p == r) break;
+        __stcg(G + x, er);   // x is not a root: no link can target it
+        x = p;
+    }
+    return r;
 }
 
 __device__ __forceinline__ void gunion(int *G, int a, int b, int *err) {
@@ -264,20 +270,6 @@ __device__ __forceinline__ void gunion(int *G, int a, int b, int *err) {
         if (atomicCAS(G + b, eb, ea) == eb) return;
     }
     atomicOr(err, kErrGlobUnion);
-}
-
-// Read-only root lookup for the link phase: follows parent pointers until a
-// root (label 1 + root) or a node whose owner already wrote its final label.
-__device__ __forceinline__ int gresolve(const int *G, int x, int *err) {
-    for (int it = 0; it < kGlobLoopCap; ++it) {
-        int v = gload(G + x);
-        if (v >= 0) return v;
-        int p = (int)((uint32_t)v & ~kEncBit);
-        if (p == x) return x + 1;
-        x = p;
-    }
-    atomicOr(err, kErrResolve);
-    return 0;
 }
 
 }  // namespace ccl

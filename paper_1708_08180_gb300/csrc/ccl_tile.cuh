@@ -127,24 +127,34 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     }
     __syncthreads();
 
-    // ---- a-2: unions between strip s-1 and strip s, one per touching run pair ----
-    if (s > 0) {
+    // ---- a-2: union-find over the segments of the tile ----
+    // Contacts join strip s-1 and strip s only.  (1) Every segment takes its
+    // first contact as parent (a CAS on a segment that is still its own
+    // parent): a forest whose edges all point one strip up, so each tree's
+    // root is its smallest key.  (2) Pointer jumping, in lock-step rounds,
+    // flattens that forest.  (3) The contacts are walked again and only pairs
+    // whose roots still differ are unioned (CAS link of the larger-key root
+    // under the smaller).  (4) Every node is pointed straight at its root.
+    auto contacts = [&](auto &&f) {
+        if (s == 0) return;
         const int up = tid - NW;
         const uint32_t av = sm.bot[up];
         const uint32_t bv = sm.top[tid];
+        if (!bv) return;
         const uint32_t aL = w > 0 ? (sm.bot[up - 1] >> 31) : 0u;
         const uint32_t bL = w > 0 ? (sm.top[tid - 1] >> 31) : 0u;
         const int baseA = sm.base[up];
         const uint32_t stA = sm.st[up];
         const uint32_t o = av & bv;
-        const uint32_t os = o & ~((o << 1) | (aL & bL));
+        uint32_t os = o & ~((o << 1) | (aL & bL));
         int la = -1, lb = -1;
-        uint32_t rem = os;
-        while (rem) {
-            const int x = __ffs(rem) - 1;
-            rem &= rem - 1;
-            const int ra = seg_rank(baseA, stA, x), rb = seg_rank(base, st, x);
-            if (ra != la || rb != lb) { sunion(sm.P, sm.K, ra, rb, err); la = ra; lb = rb; }
+        auto emit = [&](int ra, int rb) {
+            if (ra != la || rb != lb) { f(ra, rb); la = ra; lb = rb; }
+        };
+        while (os) {
+            const int x = __ffs(os) - 1;
+            os &= os - 1;
+            emit(seg_rank(baseA, stA, x), seg_rank(base, st, x));
         }
         if (HS == 2) {
             const uint32_t aR = w < NW - 1 ? (sm.bot[up + 1] & 1u) : 0u;
@@ -157,22 +167,39 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             while (dr) {
                 const int x = __ffs(dr) - 1;
                 dr &= dr - 1;
-                const int ra = seg_rank(baseA, stA, x - 1), rb = seg_rank(base, st, x);
-                if (ra != la || rb != lb) { sunion(sm.P, sm.K, ra, rb, err); la = ra; lb = rb; }
+                emit(seg_rank(baseA, stA, x - 1), seg_rank(base, st, x));
             }
             while (dl) {
                 const int x = __ffs(dl) - 1;
                 dl &= dl - 1;
-                const int ra = (x == 31) ? (baseA + __popc(stA) + (int)stA_next0 - 1)
-                                         : seg_rank(baseA, stA, x + 1);
-                const int rb = seg_rank(base, st, x);
-                if (ra != la || rb != lb) { sunion(sm.P, sm.K, ra, rb, err); la = ra; lb = rb; }
+                emit((x == 31) ? (baseA + __popc(stA) + (int)stA_next0 - 1)
+                               : seg_rank(baseA, stA, x + 1),
+                     seg_rank(base, st, x));
             }
         }
+    };
+    volatile int *vP = sm.P;
+    // (1) first contact becomes the parent
+    contacts([&](int ra, int rb) { atomicCAS(&sm.P[rb], rb, ra); });
+    __syncthreads();
+    // (2) pointer jumping until every node points at its tree's root
+    for (int round = 0; round < 64; ++round) {
+        int changed = 0;
+        for (int n = tid; n < total; n += kThreads) {
+            const int p = vP[n];
+            const int gp = vP[p];
+            if (gp != p) { vP[n] = gp; changed = 1; }
+        }
+        if (!__syncthreads_or(changed)) break;
     }
+    // (3) the remaining joins between trees
+    contacts([&](int ra, int rb) {
+        const int pa = vP[ra], pb = vP[rb];
+        if (pa != pb) sunion(sm.P, sm.K, pa, pb, err);
+    });
     __syncthreads();
 
-    // ---- roots: every node points straight at its root ----
+    // ---- (4) roots: every node points straight at its root ----
     // Read-only finds: a path-halving store by one thread could otherwise land
     // after another thread's root store and leave a non-root parent behind.
     for (int n = tid; n < total; n += kThreads) sm.P[n] = sfind_ro(sm.P, n, err);
@@ -265,19 +292,45 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
 }
 
 // ---------------------------------------------------------------------------
-// Kernel 2 body: seam unions (§II-B).  Work item `idx` in
-// [0, (tiles_y-1)*nwg) is one word of a horizontal seam (rows y-1, y with
-// y = ty*TH); the rest, (tiles_x-1)*tiles_y*NS items, are one strip of a
-// vertical seam.  Each touching pair of runs across the seam is unioned once.
+// Kernel 2 body: seam unions (§II-B).  Work items: the horizontal seams'
+// words (rows y-1, y with y = ty*TH), (tiles_y-1)*nwg of them, padded to a
+// multiple of 256 so that no warp or 256-item chunk mixes the two kinds; then
+// one item per strip of each vertical seam, (tiles_x-1)*tiles_y*NS.  Each
+// touching pair of runs across a seam is unioned once per item; on vertical
+// seams a warp (32 consecutive strips of one seam) first drops duplicate
+// pairs, which are the rule when one component crosses the seam many times.
 __device__ __forceinline__ uint32_t bit_at(const uint32_t *bits, int nwg, int y, int x) {
     return (__ldcg(bits + (size_t)y * nwg + (x >> 5)) >> (x & 31)) & 1u;
 }
 
-__device__ __forceinline__ void seam_item(const ImageArgs &a, long long idx, int *err) {
+__host__ __device__ inline long long seam_h_items(const Geom &g) {
+    return ((long long)(g.tiles_y - 1) * g.nwg + 255) / 256 * 256;
+}
+
+__host__ __device__ inline long long seam_items(const Geom &g) {
+    return seam_h_items(g) + (long long)(g.tiles_x - 1) * g.tiles_y * g.ns;
+}
+
+// union (ka, kb) unless another lane of the warp holds the same pair and a
+// lower lane id; all 32 lanes must call it (valid = false to abstain)
+__device__ __forceinline__ void warp_dedup_union(int *G, bool valid, int ka, int kb, int *err) {
+    const unsigned long long key =
+        valid ? (((unsigned long long)(uint32_t)ka << 32) | (uint32_t)kb) : ~0ull;
+    const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
+    const int lane = threadIdx.x & 31;
+    if (valid && (__ffs(same) - 1) == lane) gunion(G, ka, kb, err);
+}
+
+// `idx` may lie past the last item (then the lane only takes part in the
+// warp-wide steps); items of one warp are all horizontal or all vertical.
+__device__ __forceinline__ void seam_item(const ImageArgs &a, long long idx, long long nitems,
+                                          int *err) {
     const Geom &g = a.g;
-    const long long nh = (long long)(g.tiles_y - 1) * g.nwg;
+    const long long nh_real = (long long)(g.tiles_y - 1) * g.nwg;
+    const long long nh = seam_h_items(g);
     int *G = a.labels;
     if (idx < nh) {
+        if (idx >= nh_real) return;
         const int ty = (int)(idx / g.nwg) + 1;
         const int j = (int)(idx % g.nwg);
         const int y = ty * g.th;
@@ -293,10 +346,13 @@ __device__ __forceinline__ void seam_item(const ImageArgs &a, long long idx, int
         const int *tbase_dn = a.tws + (size_t)ty * g.tiles_x * g.tile_ints + g.off_rec;
         auto rec_up = [&](int xg) { return __ldcg(tbase_up + (size_t)(xg >> g.log2tw) * g.tile_ints + (xg & (g.tw - 1))); };
         auto rec_dn = [&](int xg) { return __ldcg(tbase_dn + (size_t)(xg >> g.log2tw) * g.tile_ints + (xg & (g.tw - 1))); };
-        int la = -1, lb = -1;
+        // the last few distinct pairs seen by this item
+        int pa0 = -1, pb0 = -1, pa1 = -1, pb1 = -1;
         auto contact = [&](int xa, int xb) {
             const int ka = rec_up(xa), kb = rec_dn(xb);
-            if (ka != la || kb != lb) { gunion(G, ka, kb, err); la = ka; lb = kb; }
+            if ((ka == pa0 && kb == pb0) || (ka == pa1 && kb == pb1)) return;
+            gunion(G, ka, kb, err);
+            pa1 = pa0; pb1 = pb0; pa0 = ka; pb0 = kb;
         };
         const uint32_t o = av & bv;
         uint32_t os = o & ~((o << 1) | (aL & bL));
@@ -310,34 +366,54 @@ __device__ __forceinline__ void seam_item(const ImageArgs &a, long long idx, int
         }
         return;
     }
-    idx -= nh;
-    const int s = (int)(idx % g.ns);
-    const long long t = idx / g.ns;
+    // vertical seams: every lane reaches the three warp-wide dedup steps
+    const long long v = idx - nh;
+    bool live = idx < nitems;
+    const int s = (int)(v % g.ns);
+    const long long t = v / g.ns;
     const int ty = (int)(t % g.tiles_y);
     const int tx = (int)(t / g.tiles_y) + 1;
     const int x = tx * g.tw;
     const int r0 = ty * g.th + s * g.hs;
-    if (r0 >= g.H) return;
-    const int *recL = a.tws + ((size_t)ty * g.tiles_x + (tx - 1)) * g.tile_ints + g.off_rec + 2 * g.tw + g.ns;
-    const int *recR = a.tws + ((size_t)ty * g.tiles_x + tx) * g.tile_ints + g.off_rec + 2 * g.tw;
-    const uint32_t l0 = bit_at(a.bits, g.nwg, r0, x - 1), r0b = bit_at(a.bits, g.nwg, r0, x);
-    uint32_t l1 = 0, r1b = 0;
-    if (g.hs == 2 && r0 + 1 < g.H) {
-        l1 = bit_at(a.bits, g.nwg, r0 + 1, x - 1);
-        r1b = bit_at(a.bits, g.nwg, r0 + 1, x);
+    live = live && r0 < g.H;
+    int kL = -1, kR = -1, kLu = -1, kRu = -1;
+    uint32_t l0 = 0, l1 = 0, rr0 = 0, rr1 = 0, lu = 0, ru = 0;
+    if (live) {
+        const int *recL = a.tws + ((size_t)ty * g.tiles_x + (tx - 1)) * g.tile_ints + g.off_rec + 2 * g.tw + g.ns;
+        const int *recR = a.tws + ((size_t)ty * g.tiles_x + tx) * g.tile_ints + g.off_rec + 2 * g.tw;
+        l0 = bit_at(a.bits, g.nwg, r0, x - 1);
+        rr0 = bit_at(a.bits, g.nwg, r0, x);
+        if (g.hs == 2 && r0 + 1 < g.H) {
+            l1 = bit_at(a.bits, g.nwg, r0 + 1, x - 1);
+            rr1 = bit_at(a.bits, g.nwg, r0 + 1, x);
+        }
+        kL = __ldcg(recL + s);
+        kR = __ldcg(recR + s);
+        if (g.hs == 2 && s > 0) {
+            // diagonals between the last row of strip s-1 and the first of strip s
+            lu = bit_at(a.bits, g.nwg, r0 - 1, x - 1);
+            ru = bit_at(a.bits, g.nwg, r0 - 1, x);
+            kLu = __ldcg(recL + s - 1);
+            kRu = __ldcg(recR + s - 1);
+        }
     }
-    if ((l0 | l1) && (r0b | r1b)) gunion(G, __ldcg(recL + s), __ldcg(recR + s), err);
-    if (g.hs == 2 && s > 0) {
-        // diagonals between the last row of strip s-1 and the first of strip s
-        const uint32_t lu = bit_at(a.bits, g.nwg, r0 - 1, x - 1);
-        const uint32_t ru = bit_at(a.bits, g.nwg, r0 - 1, x);
-        if (lu && r0b) gunion(G, __ldcg(recL + s - 1), __ldcg(recR + s), err);
-        if (l0 && ru) gunion(G, __ldcg(recL + s), __ldcg(recR + s - 1), err);
-    }
+    warp_dedup_union(G, live && (l0 | l1) && (rr0 | rr1), kL, kR, err);
+    warp_dedup_union(G, live && lu && rr0, kLu, kR, err);
+    warp_dedup_union(G, live && l0 && ru, kL, kRu, err);
 }
 
-__host__ __device__ inline long long seam_items(const Geom &g) {
-    return (long long)(g.tiles_y - 1) * g.nwg + (long long)(g.tiles_x - 1) * g.tiles_y * g.ns;
+// ---------------------------------------------------------------------------
+// Resolve body (end of §II-B): the final label (1 + global root) of every
+// border root of tile `tile`, written over its slot in the border list, with
+// full path compression of the global array.  Run by one warp per tile after
+// all seam unions.
+__device__ __forceinline__ void resolve_tile(const ImageArgs &a, int tile, int lane, int *err) {
+    int *tw_ = a.tws + (size_t)tile * a.g.tile_ints;
+    const int nb = min(__ldcg(tw_), a.g.border_cap);
+    for (int j = lane; j < nb; j += 32) {
+        const int key = __ldcg(tw_ + a.g.off_border + j);
+        tw_[a.g.off_border + j] = 1 + gfind(a.labels, key, err);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -372,8 +448,8 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
 
     const int *tw_ = a.tws + (size_t)tile * g.tile_ints;
     for (int n = tid; n < total; n += kThreads) sm.S[n] = __ldcg(tw_ + kHdrInts + n);
-    const int nb = min(__ldcg(tw_), kBorderCapMax);
-    for (int j = tid; j < nb; j += kThreads) sm.R[j] = gresolve(a.labels, __ldcg(tw_ + g.off_border + j), err);
+    const int nb = min(__ldcg(tw_), g.border_cap);
+    for (int j = tid; j < nb; j += kThreads) sm.R[j] = __ldcg(tw_ + g.off_border + j);
     __syncthreads();
     for (int n = tid; n < total; n += kThreads) {
         const int v = sm.S[n];
