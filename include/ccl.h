@@ -72,12 +72,35 @@ const char *ccl_status_string(int status);
 
 /* Tile widths the kernels support: 32, 64, 128 or 256 pixels.  A tile always
  * holds 256 strips x words; its height is (8192 / tile_w) rows for
- * 4-connectivity and twice that for 8-connectivity.  0 = library default
- * for the image size (the autotuned table). */
+ * 4-connectivity and twice that for 8-connectivity.  The default for an image
+ * comes from a process-wide size-class table (below), capped at the smallest
+ * power of two >= width.  Returns 0 on invalid arguments. */
 int ccl_default_tile_width(int height, int width, int connectivity);
 
-/* Bytes of workspace ccl_label / ccl_label_tiled need for this image and tile
- * width (tile_w 0 = default).  0 on invalid arguments. */
+/* Size-class table.  Heights and widths fall in CCL_TILE_CLASSES classes:
+ * class 0 = extent <= 64, class c = extent in (64*2^(c-1), 64*2^c], the last
+ * class = extent > 2048.  widths[hc * CCL_TILE_CLASSES + wc] is the tile width
+ * used for height class hc and width class wc (host array of
+ * CCL_TILE_CLASSES^2 ints).  get reports the effective widths at each class's
+ * representative size; set validates every entry (32/64/128/256) before
+ * installing any.  Results never depend on the table, only speed does. */
+#define CCL_TILE_CLASSES 7
+ccl_status ccl_get_tile_table(int connectivity, int *widths);
+ccl_status ccl_set_tile_table(int connectivity, const int *widths);
+
+/* Autotuner: for every class pair, label a synthetic image of the class's
+ * representative size (64*2^c, 4096 for the last class; foreground drawn with
+ * probability 1/2 on the device) with each admissible tile width, `reps`
+ * timed runs after one warm-up (CUDA events on `stream`), and install the
+ * fastest width.  Allocates its own scratch (cudaMalloc, freed before
+ * returning) and blocks until done.  CCL_OK, CCL_ERR_INVALID_ARG, CCL_ERR_OOM
+ * or CCL_ERR_CUDA. */
+ccl_status ccl_autotune(int connectivity, int reps, ccl_stream stream);
+
+/* Bytes of workspace ccl_label needs for this image: the largest need over
+ * every tile width, so a workspace sized once stays valid if the size-class
+ * table changes.  ccl_workspace_bytes_tiled: the need for one tile width
+ * (tile_w 0 = the current default).  0 on invalid arguments. */
 size_t ccl_workspace_bytes(int height, int width, int connectivity);
 size_t ccl_workspace_bytes_tiled(int height, int width, int connectivity, int tile_w);
 

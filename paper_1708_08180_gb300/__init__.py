@@ -24,7 +24,7 @@ __all__ = [
     "ccl_label_batched", "ccl_workspace_bytes", "ccl_workspace_bytes_tiled",
     "ccl_batched_workspace_bytes", "ccl_default_tile_width", "ccl_seam_pair_count", "ccl_sync",
     "ccl_shutdown", "ccl_status_string", "ccl_set_phase_events", "ccl_label_static", "Server",
-    "load",
+    "ccl_get_tile_table", "ccl_set_tile_table", "ccl_autotune", "load",
 ]
 
 
@@ -197,6 +197,31 @@ def ccl_set_phase_events(events) -> None:
             e.record()
     arr = (ctypes.c_void_p * 4)(*[int(e.cuda_event) for e in events])
     load().ccl_set_phase_events(arr)
+
+
+def ccl_get_tile_table(conn: int = 8) -> List[List[int]]:
+    """The size-class table as rows (height class) of tile widths (width class)."""
+    from ._lib import CCL_TILE_CLASSES as n
+
+    arr = (ctypes.c_int * (n * n))()
+    check(load().ccl_get_tile_table(conn, arr), "ccl_get_tile_table")
+    return [list(arr[r * n:(r + 1) * n]) for r in range(n)]
+
+
+def ccl_set_tile_table(conn: int, table: Sequence[Sequence[int]]) -> None:
+    from ._lib import CCL_TILE_CLASSES as n
+
+    flat = [int(v) for row in table for v in row]
+    if len(flat) != n * n:
+        raise ValueError(f"table must be {n}x{n}")
+    arr = (ctypes.c_int * (n * n))(*flat)
+    check(load().ccl_set_tile_table(conn, arr), "ccl_set_tile_table")
+
+
+def ccl_autotune(conn: int = 8, reps: int = 3, stream=None) -> List[List[int]]:
+    """Measure and install the fastest tile width per size class; returns the table."""
+    check(load().ccl_autotune(conn, reps, _stream_handle(stream)), "ccl_autotune")
+    return ccl_get_tile_table(conn)
 
 
 def ccl_shutdown() -> None:

@@ -26,6 +26,7 @@ CCL_ERR_NOT_FOUND = 7
 CCL_ERR_PENDING = 8
 CCL_FLAG_LOCAL_ONLY = 1
 CCL_STATIC_SCRATCH_BYTES = 64 << 20
+CCL_TILE_CLASSES = 7
 
 
 class CclError(RuntimeError):
@@ -59,6 +60,9 @@ _SIGS = {
     "ccl_label_static": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_int, _P]),
     "ccl_seam_pair_count": (_c.c_longlong, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int]),
     "ccl_sync": (_c.c_int, [_P]),
+    "ccl_get_tile_table": (_c.c_int, [_c.c_int, _c.POINTER(_c.c_int)]),
+    "ccl_set_tile_table": (_c.c_int, [_c.c_int, _c.POINTER(_c.c_int)]),
+    "ccl_autotune": (_c.c_int, [_c.c_int, _c.c_int, _P]),
     "ccl_set_phase_events": (None, [_c.POINTER(_P)]),
     "ccl_shutdown": (_c.c_int, []),
     "ccl_batched_workspace_bytes": (_c.c_size_t, [_c.POINTER(ccl_image), _c.c_int, _c.c_int]),

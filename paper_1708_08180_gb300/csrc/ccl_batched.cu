@@ -193,7 +193,9 @@ bool plan(const ccl_image *imgs, int n, int conn, Layout &L) {
                                  default_tile_width(im.height, im.width, conn));
         L.geom[k] = g;
         L.img_off[k] = off;
-        off += align256(bits_bytes(g) + tiles_bytes(g));
+        // sized for the widest need over all tile widths: a workspace sized
+        // before a re-tune of the size-class table stays valid after it
+        off += align256(ccl_workspace_bytes(im.height, im.width, conn));
         tiles += (long long)g.tiles_x * g.tiles_y;
         chunks += (seam_items(g) + 255) / 256;
     }

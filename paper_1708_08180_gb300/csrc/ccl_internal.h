@@ -26,7 +26,10 @@ inline bool valid_conn(int conn) { return conn == 4 || conn == 8; }
 inline bool valid_tile_w(int tw) { return tw == 32 || tw == 64 || tw == 128 || tw == 256; }
 
 // Size-class table: tile width for an image (the autotuned default).
+constexpr int kTileClasses = 7;   // extents <= 64, 128, 256, 512, 1024, 2048, > 2048
+int tile_class(int extent);
 int default_tile_width(int height, int width, int conn);
+void set_tile_table_entry(int conn, int hc, int wc, int tile_w);
 
 // Release batched-path state.
 void free_batched_state();

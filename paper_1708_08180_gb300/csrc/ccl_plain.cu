@@ -1,5 +1,8 @@
 // ccl_plain.cu -- single-image path: the three kernels (local merge, seam
 // unions, link) and the ccl_label / ccl_label_tiled entry points.
+#include <atomic>
+#include <mutex>
+
 #include "ccl_internal.h"
 #include "ccl_tile.cuh"
 
@@ -48,16 +51,46 @@ static void launch_tile_kernel(const ImageArgs &a, bool local_only, int *err, cu
 #undef CCL_CASE
 }
 
-// Size-class table.  Tiles are 8192 (4-conn) or 16384 (8-conn) pixels; the
-// widest tile that does not exceed the next power of two >= W keeps idle
-// columns low and vertical seams rare.
+// Size-class table: the tile width for an image, indexed by the classes of
+// its width and height (<= 64, 128, 256, 512, 1024, 2048, > 2048).  Tiles
+// are 8192 (4-conn) or 16384 (8-conn) pixels whatever their width, so the
+// choice trades idle columns and vertical seams (narrow tiles) against idle
+// rows and horizontal seams (wide tiles).  Initialised with the smallest
+// power of two >= W (at most 256) and re-measured by ccl_autotune().
+static std::atomic<int> g_tile_table[2][kTileClasses][kTileClasses];
+static std::once_flag g_tile_once;
+
+static int initial_tile_width(int wc) {
+    return wc <= 0 ? 64 : wc == 1 ? 128 : 256;
+}
+
+static void init_tile_table() {
+    std::call_once(g_tile_once, [] {
+        for (int c = 0; c < 2; ++c)
+            for (int hc = 0; hc < kTileClasses; ++hc)
+                for (int wc = 0; wc < kTileClasses; ++wc)
+                    g_tile_table[c][hc][wc].store(initial_tile_width(wc));
+    });
+}
+
+int tile_class(int extent) {
+    int c = 0;
+    while (c < kTileClasses - 1 && extent > (64 << c)) ++c;
+    return c;
+}
+
 int default_tile_width(int height, int width, int conn) {
-    (void)height;
-    (void)conn;
-    if (width <= 32) return 32;
-    if (width <= 64) return 64;
-    if (width <= 128) return 128;
-    return 256;
+    init_tile_table();
+    int tw = g_tile_table[conn == 8 ? 1 : 0][tile_class(height)][tile_class(width)].load();
+    // never wider than needed: the smallest power of two >= W (>= 32)
+    int cap = 32;
+    while (cap < width && cap < 256) cap <<= 1;
+    return tw < cap ? tw : cap;
+}
+
+void set_tile_table_entry(int conn, int hc, int wc, int tile_w) {
+    init_tile_table();
+    g_tile_table[conn == 8 ? 1 : 0][hc][wc].store(tile_w);
 }
 
 // per host thread: events for the next enqueue_label call (benchmark hook)
@@ -69,11 +102,15 @@ ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, in
                          cudaStream_t stream) {
     if (!d_img || !d_labels || !valid_image_dims(height, width) || !valid_conn(conn))
         return CCL_ERR_INVALID_ARG;
-    if (tile_w == 0) tile_w = default_tile_width(height, width, conn);
+    const bool default_tile = tile_w == 0;
+    if (default_tile) tile_w = default_tile_width(height, width, conn);
     if (!valid_tile_w(tile_w)) return CCL_ERR_INVALID_ARG;
     if (flags & ~(unsigned)CCL_FLAG_LOCAL_ONLY) return CCL_ERR_INVALID_ARG;
     const Geom g = make_geom(height, width, conn, tile_w);
-    const size_t need = bits_bytes(g) + tiles_bytes(g);
+    // the documented contract: ccl_workspace_bytes() for the default tile
+    // width (it does not depend on the current table), the exact need otherwise
+    const size_t need = default_tile ? ccl_workspace_bytes(height, width, conn)
+                                     : bits_bytes(g) + tiles_bytes(g);
     ccl_status st = CCL_OK;
     if (!d_ws) {
         d_ws = library_workspace(stream, need, &st);
@@ -128,8 +165,15 @@ extern "C" size_t ccl_workspace_bytes_tiled(int height, int width, int connectiv
     return ccl::bits_bytes(g) + ccl::tiles_bytes(g);
 }
 
+// The largest need over every tile width, so that a workspace sized once
+// stays large enough when the size-class table is re-tuned.
 extern "C" size_t ccl_workspace_bytes(int height, int width, int connectivity) {
-    return ccl_workspace_bytes_tiled(height, width, connectivity, 0);
+    size_t m = 0;
+    for (int tw = 32; tw <= 256; tw <<= 1) {
+        const size_t b = ccl_workspace_bytes_tiled(height, width, connectivity, tw);
+        if (b > m) m = b;
+    }
+    return m;
 }
 
 extern "C" ccl_status ccl_label(const uint8_t *d_img, int32_t *d_labels, int height, int width,

@@ -122,3 +122,28 @@ def test_server_create_without_gpu_fails_cleanly(lib):
     st = lib.ccl_server_create(ctypes.byref(cfg), ctypes.byref(h))
     assert st in (_lib.CCL_ERR_CUDA, _lib.CCL_ERR_INVALID_ARG)
     assert not h.value
+
+
+def test_tile_table_get_set_roundtrip(lib):
+    n = _lib.CCL_TILE_CLASSES
+    before = ccl.ccl_get_tile_table(8)
+    assert len(before) == n and all(len(r) == n for r in before)
+    # effective widths never exceed the class's need (<= 64 wide -> <= 64)
+    assert all(w <= 64 for w in [row[0] for row in before])
+    try:
+        table = [[32] * n for _ in range(n)]
+        ccl.ccl_set_tile_table(8, table)
+        assert ccl.ccl_default_tile_width(4096, 4096, 8) == 32
+        assert ccl.ccl_default_tile_width(4096, 4096, 4) == before_4096(lib)
+        with pytest.raises(ccl.CclError):
+            ccl.ccl_set_tile_table(8, [[48] * n for _ in range(n)])
+        assert ccl.ccl_default_tile_width(4096, 4096, 8) == 32   # nothing installed on error
+    finally:
+        ccl.ccl_set_tile_table(8, [[256] * n for _ in range(n)])
+    # workspace sizing covers every tile width
+    for tw in (32, 64, 128, 256):
+        assert ccl.ccl_workspace_bytes_tiled(1000, 3000, 8, tw) <= ccl.ccl_workspace_bytes(1000, 3000, 8)
+
+
+def before_4096(lib):
+    return lib.ccl_default_tile_width(4096, 4096, 4)
