@@ -18,7 +18,10 @@ Also reported:
   e2e           the same metric through the server's C ABI with pinned HOST
                 buffers: host-to-device copy + labelling + device-to-host copy;
   cpu_baseline  the CPU oracle (single-threaded BFS) on a bounded sample;
-  clocks        nvidia-smi samples taken during the timed region.
+  clocks        nvidia-smi samples taken during the timed region;
+  batched       256 images of 64..2048: one batched call vs 256 plain calls;
+  served        Poisson request streams: the server vs one plain call per
+                request, p50/p99 latency and throughput.
 
 ``--impl reference`` times the CPU oracle itself as the reference arm.
 """
@@ -272,6 +275,149 @@ def e2e_server(img_np, steps: int, device_index: int):
             "server_p50_ms": stats["p50_ms"], "server_p99_ms": stats["p99_ms"]}
 
 
+def batched_vs_plain(device_index: int, seed: int = 0, reps: int = 10):
+    """The batched configuration: 256 images, sides log-uniform in 64..2048,
+    p ~ U(0.3, 0.7), 8-connectivity.  One batched call (graph replay) against
+    256 plain ccl_label calls on one stream, device time by CUDA events, median
+    of `reps`."""
+    import torch
+
+    import paper_1708_08180_gb300 as ccl
+    import synthetic
+
+    dev = torch.device("cuda", device_index)
+    host = synthetic.batch_images(seed)
+    imgs = [torch.from_numpy(h).to(dev) for h in host]
+    outs = [torch.empty(tuple(i.shape), dtype=torch.int32, device=dev) for i in imgs]
+    px = sum(h.size for h in host)
+    ws_b = torch.empty(ccl.ccl_batched_workspace_bytes(imgs, 8), dtype=torch.uint8, device=dev)
+    ws_p = torch.empty(max(ccl.ccl_workspace_bytes(*h.shape, 8) for h in host),
+                       dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def time_it(fn):
+        ts = []
+        for r in range(reps + 2):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            if r >= 2:
+                ts.append(a.elapsed_time(b))
+        ts.sort()
+        return ts[len(ts) // 2], ts[min(len(ts) - 1, int(round(0.99 * (len(ts) - 1))))]
+
+    def plain():
+        for i, o in zip(imgs, outs):
+            ccl.ccl_label(i, 8, out=o, ws=ws_p, stream=stream)
+
+    def batched():
+        ccl.ccl_label_batched(imgs, 8, outs=outs, ws=ws_b, stream=stream)
+
+    tb, tb99 = time_it(batched)
+    tp, tp99 = time_it(plain)
+    ccl.ccl_sync(stream)
+    return {"images": len(host), "pixels": px,
+            "batched_gpix_s": px / (tb / 1e3) / 1e9, "batched_ms": tb, "batched_p99_ms": tb99,
+            "plain_gpix_s": px / (tp / 1e3) / 1e9, "plain_ms": tp, "plain_p99_ms": tp99,
+            "speedup": tp / tb}
+
+
+def served_vs_plain(device_index: int, rates=(2000.0, 10000.0), seconds: float = 1.0,
+                    seed: int = 0):
+    """Serving: Poisson arrivals; 50 % 1920x1080 smoothed-noise video frames,
+    50 % squares log-uniform 128..4096, Bernoulli 0.5, 8-connectivity.  The
+    continuous-batching server against one plain call per request (H2D,
+    ccl_label, D2H, synchronise) replaying the same trace.  Latency = scheduled
+    arrival -> labels in pinned host memory."""
+    import numpy as np
+    import torch
+
+    import paper_1708_08180_gb300 as ccl
+    import synthetic
+
+    dev = torch.device("cuda", device_index)
+    frames = synthetic.video_frames(16, seed)
+    rng = np.random.default_rng(seed)
+    sides = np.rint(np.exp(rng.uniform(np.log(128), np.log(4096), 16))).astype(int)
+    squares = [synthetic.bernoulli(int(sd), int(sd), 0.5, k, cfg_id=synthetic.CFG_SERVE)
+               for k, sd in enumerate(sides)]
+    pool = {"frame": [torch.from_numpy(f).pin_memory() for f in frames],
+            "square": [torch.from_numpy(q).pin_memory() for q in squares]}
+    pool_out = {k: [torch.empty(tuple(t.shape), dtype=torch.int32).pin_memory() for t in v]
+                for k, v in pool.items()}
+    out = {}
+    for rate in rates:
+        trace = synthetic.serving_trace(rate, max(1, int(rate * seconds)), seed)
+        items = []
+        for k, (t_arr, kind, h, w) in enumerate(trace):
+            j = k % 16
+            items.append((t_arr, pool[kind][j], pool_out[kind][j]))
+        px = sum(int(i[1].numel()) for i in items)
+
+        # server
+        lat = [0.0] * len(items)
+        with ccl.Server(conn=8, max_batch=64, max_inflight=3, device=device_index) as srv:
+            srv.wait(srv.submit(items[0][1], items[0][2]))          # warm-up
+            ids = [None] * len(items)
+            done_t = [0.0] * len(items)
+            t0 = time.perf_counter()
+
+            def waiter():
+                for k in range(len(items)):
+                    while ids[k] is None:
+                        time.sleep(2e-5)
+                    srv.wait(ids[k])
+                    done_t[k] = time.perf_counter() - t0
+
+            th = threading.Thread(target=waiter)
+            th.start()
+            for k, (t_arr, src, dst) in enumerate(items):
+                now = time.perf_counter() - t0
+                if t_arr > now:
+                    time.sleep(t_arr - now)
+                ids[k] = srv.submit(src, dst)
+            th.join()
+            for k in range(len(items)):
+                lat[k] = (done_t[k] - items[k][0]) * 1e3
+            span = max(done_t) - items[0][0]
+        srv_res = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                   "gpix_s": px / span / 1e9}
+
+        # plain: one ccl_label per request, in arrival order, one stream
+        stream = torch.cuda.Stream(dev)
+        maxpx = max(int(i[1].numel()) for i in items)
+        d_in = torch.empty(maxpx, dtype=torch.uint8, device=dev)
+        d_out = torch.empty(maxpx, dtype=torch.int32, device=dev)
+        ws = torch.empty(max(ccl.ccl_workspace_bytes(*i[1].shape, 8) for i in items),
+                         dtype=torch.uint8, device=dev)
+        lat_p = []
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for t_arr, src, dst in items:
+                now = time.perf_counter() - t0
+                if t_arr > now:
+                    time.sleep(t_arr - now)
+                h, w = src.shape
+                di = d_in[:h * w].view(h, w)
+                do = d_out[:h * w].view(h, w)
+                di.copy_(src, non_blocking=True)
+                ccl.ccl_label(di, 8, out=do, ws=ws, stream=stream)
+                dst.copy_(do, non_blocking=True)
+                stream.synchronize()
+                lat_p.append((time.perf_counter() - t0 - t_arr) * 1e3)
+        span_p = time.perf_counter() - t0 - items[0][0]
+        ccl.ccl_sync(stream)
+        out[str(int(rate))] = {
+            "requests": len(items), "offered_gpix_s": px / (items[-1][0] - items[0][0] + 1e-9) / 1e9,
+            "server": srv_res,
+            "plain": {"p50_ms": float(np.percentile(lat_p, 50)),
+                      "p99_ms": float(np.percentile(lat_p, 99)), "gpix_s": px / span_p / 1e9}}
+    return out
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -377,6 +523,10 @@ def run_ours(args, rank, world, local):
     }
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e_server(host_imgs[0], K, local)
+    if rank == 0 and not args.no_batched:
+        line["batched"] = batched_vs_plain(local)
+    if rank == 0 and not args.no_served:
+        line["served"] = served_vs_plain(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(host_imgs[0])
     if rank == 0:
@@ -396,6 +546,10 @@ def main(argv=None) -> int:
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-vs-plain leg (256 images of 64..2048)")
+    ap.add_argument("--no-served", action="store_true",
+                    help="skip the served-vs-plain leg (Poisson arrivals)")
     ap.add_argument("--size", type=int, default=8192, help="image side (default 8192)")
     ap.add_argument("--density", type=float, default=0.5, help="Bernoulli p (default 0.5)")
     ap.add_argument("--conn", type=int, choices=(4, 8), default=8)

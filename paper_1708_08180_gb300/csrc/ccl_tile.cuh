@@ -32,8 +32,11 @@ struct SmemMerge {
 
 // Shared memory of the link phase.
 struct SmemLink {
-    int S[kNodeCap];          // label per segment node
-    int R[kBorderCapMax];        // resolved label per border root
+    int S[kNodeCap];              // label per segment node
+    int R[kBorderCapMax];         // final label per border root
+    uint32_t rows[2 * kThreads];  // bit rows of the tile: [row][word]
+    uint32_t st[kThreads];        // segment starts per (strip, word)
+    int base[kThreads];           // rank of the word's first segment start
     int warp_sums[kThreads / 32];
 };
 
@@ -296,9 +299,9 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
 // words (rows y-1, y with y = ty*TH), (tiles_y-1)*nwg of them, padded to a
 // multiple of 256 so that no warp or 256-item chunk mixes the two kinds; then
 // one item per strip of each vertical seam, (tiles_x-1)*tiles_y*NS.  Each
-// touching pair of runs across a seam is unioned once per item; on vertical
-// seams a warp (32 consecutive strips of one seam) first drops duplicate
-// pairs, which are the rule when one component crosses the seam many times.
+// touching pair of runs across a seam yields one union of the two local roots;
+// a warp (32 consecutive words or strips of one seam) drops equal pairs first,
+// which are the rule when one component crosses the seam many times.
 __device__ __forceinline__ uint32_t bit_at(const uint32_t *bits, int nwg, int y, int x) {
     return (__ldcg(bits + (size_t)y * nwg + (x >> 5)) >> (x & 31)) & 1u;
 }
@@ -330,39 +333,56 @@ __device__ __forceinline__ void seam_item(const ImageArgs &a, long long idx, lon
     const long long nh = seam_h_items(g);
     int *G = a.labels;
     if (idx < nh) {
-        if (idx >= nh_real) return;
-        const int ty = (int)(idx / g.nwg) + 1;
-        const int j = (int)(idx % g.nwg);
-        const int y = ty * g.th;
-        const uint32_t *ra_ = a.bits + (size_t)(y - 1) * g.nwg;
-        const uint32_t *rb_ = a.bits + (size_t)y * g.nwg;
-        const uint32_t av = __ldcg(ra_ + j), bv = __ldcg(rb_ + j);
-        if (!bv) return;   // every contact needs a pixel in row y
-        const uint32_t aL = j > 0 ? (__ldcg(ra_ + j - 1) >> 31) : 0u;
-        const uint32_t bL = j > 0 ? (__ldcg(rb_ + j - 1) >> 31) : 0u;
-        const uint32_t aR = j < g.nwg - 1 ? (__ldcg(ra_ + j + 1) & 1u) : 0u;
-        const uint32_t bR = j < g.nwg - 1 ? (__ldcg(rb_ + j + 1) & 1u) : 0u;
-        const int *tbase_up = a.tws + (size_t)(ty - 1) * g.tiles_x * g.tile_ints + g.off_rec + g.tw;
-        const int *tbase_dn = a.tws + (size_t)ty * g.tiles_x * g.tile_ints + g.off_rec;
+        // horizontal seams; all 32 lanes take part in every warp-wide step
+        const bool live = idx < nh_real;
+        const int ty = live ? (int)(idx / g.nwg) + 1 : 1;
+        const int j = live ? (int)(idx % g.nwg) : 0;
+        uint32_t os = 0, dr = 0, dl = 0;
+        const int *tbase_up = nullptr, *tbase_dn = nullptr;
+        if (live) {
+            const int y = ty * g.th;
+            const uint32_t *ra_ = a.bits + (size_t)(y - 1) * g.nwg;
+            const uint32_t *rb_ = a.bits + (size_t)y * g.nwg;
+            const uint32_t av = __ldcg(ra_ + j), bv = __ldcg(rb_ + j);
+            if (bv) {   // every contact needs a pixel in row y
+                const uint32_t aL = j > 0 ? (__ldcg(ra_ + j - 1) >> 31) : 0u;
+                const uint32_t bL = j > 0 ? (__ldcg(rb_ + j - 1) >> 31) : 0u;
+                const uint32_t aR = j < g.nwg - 1 ? (__ldcg(ra_ + j + 1) & 1u) : 0u;
+                const uint32_t bR = j < g.nwg - 1 ? (__ldcg(rb_ + j + 1) & 1u) : 0u;
+                const uint32_t o = av & bv;
+                os = o & ~((o << 1) | (aL & bL));
+                if (g.hs == 2) {
+                    dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
+                    dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31));
+                }
+            }
+            tbase_up = a.tws + (size_t)(ty - 1) * g.tiles_x * g.tile_ints + g.off_rec + g.tw;
+            tbase_dn = a.tws + (size_t)ty * g.tiles_x * g.tile_ints + g.off_rec;
+        }
         auto rec_up = [&](int xg) { return __ldcg(tbase_up + (size_t)(xg >> g.log2tw) * g.tile_ints + (xg & (g.tw - 1))); };
         auto rec_dn = [&](int xg) { return __ldcg(tbase_dn + (size_t)(xg >> g.log2tw) * g.tile_ints + (xg & (g.tw - 1))); };
-        // the last few distinct pairs seen by this item
-        int pa0 = -1, pb0 = -1, pa1 = -1, pb1 = -1;
-        auto contact = [&](int xa, int xb) {
-            const int ka = rec_up(xa), kb = rec_dn(xb);
-            if ((ka == pa0 && kb == pb0) || (ka == pa1 && kb == pb1)) return;
-            gunion(G, ka, kb, err);
-            pa1 = pa0; pb1 = pb0; pa0 = ka; pb0 = kb;
-        };
-        const uint32_t o = av & bv;
-        uint32_t os = o & ~((o << 1) | (aL & bL));
         const int xw = 32 * j;
-        while (os) { const int x = __ffs(os) - 1; os &= os - 1; contact(xw + x, xw + x); }
-        if (g.hs == 2) {
-            uint32_t dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
-            uint32_t dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31));
-            while (dr) { const int x = __ffs(dr) - 1; dr &= dr - 1; contact(xw + x - 1, xw + x); }
-            while (dl) { const int x = __ffs(dl) - 1; dl &= dl - 1; contact(xw + x + 1, xw + x); }
+        int pa = -1, pb = -1;
+        // one contact per lane per round; equal pairs across the warp (one
+        // component crossing the seam many times) are unioned by one lane
+        while (__any_sync(0xFFFFFFFFu, (os | dr | dl) != 0u)) {
+            int ka = -1, kb = -1;
+            bool have = true;
+            if (os) {
+                const int x = __ffs(os) - 1; os &= os - 1;
+                ka = rec_up(xw + x); kb = rec_dn(xw + x);
+            } else if (dr) {
+                const int x = __ffs(dr) - 1; dr &= dr - 1;
+                ka = rec_up(xw + x - 1); kb = rec_dn(xw + x);
+            } else if (dl) {
+                const int x = __ffs(dl) - 1; dl &= dl - 1;
+                ka = rec_up(xw + x + 1); kb = rec_dn(xw + x);
+            } else {
+                have = false;
+            }
+            const bool fresh = have && !(ka == pa && kb == pb);
+            if (have) { pa = ka; pb = kb; }
+            warp_dedup_union(G, fresh, ka, kb, err);
         }
         return;
     }
@@ -418,8 +438,9 @@ __device__ __forceinline__ void resolve_tile(const ImageArgs &a, int tile, int l
 
 // ---------------------------------------------------------------------------
 // Link body (§II-C): re-derive the segments of the tile from the bit image,
-// resolve the border roots through the global array, write one int32 label
-// per pixel.
+// give every segment its final label (its local root's, or the resolved label
+// of its border root), and write one int32 per pixel.  The stores are laid
+// out so that 32 lanes write 128 consecutive pixels (512 bytes) of one row.
 template <int NW, int HS>
 __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink &sm, int *err) {
     constexpr int NS = kThreads / NW;
@@ -431,67 +452,73 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
     const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
     const int x0 = tx * TW, y0 = ty * TH;
     const int gwi = x0 / 32 + w;
-    const int gx = x0 + 32 * w;
 
     uint32_t rows[HS];
 #pragma unroll
     for (int j = 0; j < HS; ++j) {
         const int y = y0 + s * HS + j;
         rows[j] = (y < g.H && gwi < g.nwg) ? __ldcg(a.bits + (size_t)y * g.nwg + gwi) : 0u;
+        sm.rows[(s * HS + j) * NW + w] = rows[j];
     }
     const uint32_t m = rows[0] | rows[HS - 1];
     uint32_t mL = __shfl_up_sync(0xFFFFFFFFu, m, 1);
     mL = (w > 0) ? (mL >> 31) : 0u;
     const uint32_t st = m & ~((m << 1) | mL);
-    int total;
-    const int base = block_excl_scan(__popc(st), sm.warp_sums, total);
-
     const int *tw_ = a.tws + (size_t)tile * g.tile_ints;
-    for (int n = tid; n < total; n += kThreads) sm.S[n] = __ldcg(tw_ + kHdrInts + n);
     const int nb = min(__ldcg(tw_), g.border_cap);
     for (int j = tid; j < nb; j += kThreads) sm.R[j] = __ldcg(tw_ + g.off_border + j);
-    __syncthreads();
+    int total;
+    const int base = block_excl_scan(__popc(st), sm.warp_sums, total);   // syncs: R visible
+    sm.st[tid] = st;
+    sm.base[tid] = base;
     for (int n = tid; n < total; n += kThreads) {
-        const int v = sm.S[n];
+        int v = __ldcg(tw_ + kHdrInts + n);
         if (v < 0) {
             const int j = -v - 1;
             if (j < nb) {
-                sm.S[n] = sm.R[j];
+                v = sm.R[j];
             } else {
-                sm.S[n] = 0;
+                v = 0;
                 atomicOr(err, kErrBorderCap);
             }
         }
+        sm.S[n] = v;
     }
     __syncthreads();
 
-    if (gx >= g.W) return;
-    const int ncol = min(32, g.W - gx);
+    const int ncols = min(TW, g.W - x0);   // valid columns of this tile
+    const int nrows = min(TH, g.H - y0);
+    if (a.out_aligned16 && (ncols & 3) == 0) {
+        // chunk = 4 pixels; a row has TW/4 chunks
+        constexpr int CPR = TW / 4;
+        for (int id = tid; id < TH * CPR; id += kThreads) {
+            const int r = id / CPR, q = id % CPR;
+            const int c0 = 4 * q;
+            if (r >= nrows || c0 >= ncols) continue;
+            const int wq = c0 >> 5, b0 = c0 & 31;
+            const int o = (r / HS) * NW + wq;
+            const uint32_t rb = sm.rows[r * NW + wq];
+            const uint32_t sq = sm.st[o];
+            int cur = sm.base[o] + __popc(sq & le_mask(b0)) - 1;
+            int v[4];
 #pragma unroll
-    for (int j = 0; j < HS; ++j) {
-        const int y = y0 + s * HS + j;
-        if (y >= g.H) break;
-        const uint32_t rb = rows[j];
-        int32_t *out = a.labels + (size_t)y * g.W + gx;
-        if (a.out_aligned16 && ncol == 32) {
-            int cur = base - 1;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                int v[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int c = 4 * q + e;
-                    cur += (st >> c) & 1u;
-                    v[e] = ((rb >> c) & 1u) ? sm.S[cur < 0 ? 0 : cur] : 0;
-                }
-                __stcs(reinterpret_cast<int4 *>(out) + q, make_int4(v[0], v[1], v[2], v[3]));
+            for (int e = 0; e < 4; ++e) {
+                if (e > 0) cur += (sq >> (b0 + e)) & 1u;
+                v[e] = ((rb >> (b0 + e)) & 1u) ? sm.S[cur < 0 ? 0 : cur] : 0;
             }
-        } else {
-            int cur = base - 1;
-            for (int c = 0; c < ncol; ++c) {
-                cur += (st >> c) & 1u;
-                out[c] = ((rb >> c) & 1u) ? sm.S[cur < 0 ? 0 : cur] : 0;
-            }
+            int32_t *out = a.labels + (size_t)(y0 + r) * g.W + x0 + c0;
+            __stcs(reinterpret_cast<int4 *>(out), make_int4(v[0], v[1], v[2], v[3]));
+        }
+    } else {
+        for (int id = tid; id < TH * TW; id += kThreads) {
+            const int r = id / TW, c = id % TW;
+            if (r >= nrows || c >= ncols) continue;
+            const int wq = c >> 5, b = c & 31;
+            const int o = (r / HS) * NW + wq;
+            const uint32_t rb = sm.rows[r * NW + wq];
+            const uint32_t sq = sm.st[o];
+            const int cur = sm.base[o] + __popc(sq & le_mask(b)) - 1;
+            a.labels[(size_t)(y0 + r) * g.W + x0 + c] = ((rb >> b) & 1u) ? sm.S[cur < 0 ? 0 : cur] : 0;
         }
     }
 }
