@@ -51,8 +51,12 @@ constexpr int kErrResolve = 16;
 constexpr int kErrBorderCap = 32;
 constexpr int kErrQueue = 64;
 
-constexpr int kSmemLoopCap = 1 << 16;
-constexpr int kGlobLoopCap = 1 << 26;
+// Every union-find walk draws on a per-thread budget of pointer hops; when it
+// runs out the thread records an error and stops, so no input and no defect
+// can keep a kernel spinning.  Valid inputs stay far below both budgets
+// (chains are shortened by path halving / compression as they are walked).
+constexpr int kSmemHopBudget = 1 << 20;   // per thread per tile (shared memory)
+constexpr int kGlobHopBudget = 1 << 20;   // per thread per work item (global memory)
 
 // Geometry of one image under one tile shape, and the layout of the per-tile
 // workspace (all offsets in ints from the tile's base):
@@ -195,43 +199,42 @@ __device__ __forceinline__ int block_excl_scan(int v, int *warp_sums, int &total
 // not required: links go from the root with the larger key to the one with
 // the smaller key, so every root is the smallest key of its tree).
 
-__device__ __forceinline__ int sfind(volatile int *P, int x, int *err) {
-    for (int it = 0; it < kSmemLoopCap; ++it) {
-        int p = P[x];
+__device__ __forceinline__ int sfind(volatile int *P, int x, int &budget, int *err) {
+    for (;;) {
+        if (--budget < 0) { atomicOr(err, kErrSmemFind); return x; }
+        const int p = P[x];
         if (p == x) return x;
-        int g = P[p];
+        const int g = P[p];
         if (g == p) return p;
-        P[x] = g;   // path halving: g is an ancestor of x
+        P[x] = g;   // path halving: g is an ancestor of x (a smaller key)
         x = g;
     }
-    atomicOr(err, kErrSmemFind);
-    return x;
 }
 
 // Read-only find, for the pass that stores every node's root: with no
 // path-halving stores, each P[n] ends the pass holding exactly its root.
-__device__ __forceinline__ int sfind_ro(volatile const int *P, int x, int *err) {
-    for (int it = 0; it < kSmemLoopCap; ++it) {
+__device__ __forceinline__ int sfind_ro(volatile const int *P, int x, int &budget, int *err) {
+    for (;;) {
+        if (--budget < 0) { atomicOr(err, kErrSmemFind); return x; }
         const int p = P[x];
         if (p == x) return x;
         x = p;
     }
-    atomicOr(err, kErrSmemFind);
-    return x;
 }
 
-__device__ __forceinline__ void sunion(int *P, const int *K, int a, int b, int *err) {
+__device__ __forceinline__ void sunion(int *P, const int *K, int a, int b, int &budget,
+                                       int *err) {
     volatile int *vP = P;
     volatile const int *vK = K;
-    for (int it = 0; it < kSmemLoopCap; ++it) {
-        a = sfind(vP, a, err);
-        b = sfind(vP, b, err);
+    for (;;) {
+        a = sfind(vP, a, budget, err);
+        b = sfind(vP, b, budget, err);
         if (a == b) return;
+        if (budget < 0) { atomicOr(err, kErrSmemUnion); return; }
         if ((vK[a] & kKeyMask) > (vK[b] & kKeyMask)) { int t = a; a = b; b = t; }
         // link root b (larger key) under root a; fails if b stopped being a root
         if (atomicCAS(&P[b], b, a) == b) return;
     }
-    atomicOr(err, kErrSmemUnion);
 }
 
 // ---------------------------------------------------------------------------
@@ -241,35 +244,40 @@ __device__ __forceinline__ void sunion(int *P, const int *K, int a, int b, int *
 
 __device__ __forceinline__ int gload(const int *p) { return __ldcg(p); }
 
-__device__ __forceinline__ int gfind(int *G, int x, int *err) {
-    // walk to the root, then point every node of the walked path at it
+__device__ __forceinline__ int gfind(int *G, int x, int &budget, int *err) {
+    // walk to the root r ...
     int r = x;
-    for (int it = 0;; ++it) {
+    for (;;) {
+        if (--budget < 0) { atomicOr(err, kErrGlobFind); return r; }
         const int p = (int)((uint32_t)gload(G + r) & ~kEncBit);
         if (p == r) break;
-        if (it >= kGlobLoopCap) { atomicOr(err, kErrGlobFind); return r; }
         r = p;
     }
+    // ... then point the walked nodes at r.  Parents always have smaller
+    // indices, so only nodes above r in index (x > r) are rewritten: a path
+    // that another thread has meanwhile compressed past r is left alone
+    // instead of being pointed back down (which would close a cycle).
     const int er = (int)((uint32_t)r | kEncBit);
-    for (int it = 0; x != r && it < kGlobLoopCap; ++it) {
+    while (x > r) {
+        if (--budget < 0) { atomicOr(err, kErrGlobFind); return r; }
         const int p = (int)((uint32_t)gload(G + x) & ~kEncBit);
-        if (p == r) break;
+        if (p <= r) break;
         __stcg(G + x, er);   // x is not a root: no link can target it
         x = p;
     }
     return r;
 }
 
-__device__ __forceinline__ void gunion(int *G, int a, int b, int *err) {
-    for (int it = 0; it < kGlobLoopCap; ++it) {
-        a = gfind(G, a, err);
-        b = gfind(G, b, err);
+__device__ __forceinline__ void gunion(int *G, int a, int b, int &budget, int *err) {
+    for (;;) {
+        a = gfind(G, a, budget, err);
+        b = gfind(G, b, budget, err);
         if (a == b) return;
+        if (budget < 0) { atomicOr(err, kErrGlobUnion); return; }
         if (a > b) { int t = a; a = b; b = t; }
         const int eb = (int)((uint32_t)b | kEncBit), ea = (int)((uint32_t)a | kEncBit);
         if (atomicCAS(G + b, eb, ea) == eb) return;
     }
-    atomicOr(err, kErrGlobUnion);
 }
 
 }  // namespace ccl

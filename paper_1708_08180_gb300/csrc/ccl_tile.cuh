@@ -182,6 +182,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         }
     };
     volatile int *vP = sm.P;
+    int budget = kSmemHopBudget;
     // (1) first contact becomes the parent
     contacts([&](int ra, int rb) { atomicCAS(&sm.P[rb], rb, ra); });
     __syncthreads();
@@ -198,14 +199,14 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     // (3) the remaining joins between trees
     contacts([&](int ra, int rb) {
         const int pa = vP[ra], pb = vP[rb];
-        if (pa != pb) sunion(sm.P, sm.K, pa, pb, err);
+        if (pa != pb) sunion(sm.P, sm.K, pa, pb, budget, err);
     });
     __syncthreads();
 
     // ---- (4) roots: every node points straight at its root ----
     // Read-only finds: a path-halving store by one thread could otherwise land
     // after another thread's root store and leave a non-root parent behind.
-    for (int n = tid; n < total; n += kThreads) sm.P[n] = sfind_ro(sm.P, n, err);
+    for (int n = tid; n < total; n += kThreads) sm.P[n] = sfind_ro(sm.P, n, budget, err);
     __syncthreads();
 
     int *tw_ = a.tws + (size_t)tile * g.tile_ints;
@@ -316,12 +317,13 @@ __host__ __device__ inline long long seam_items(const Geom &g) {
 
 // union (ka, kb) unless another lane of the warp holds the same pair and a
 // lower lane id; all 32 lanes must call it (valid = false to abstain)
-__device__ __forceinline__ void warp_dedup_union(int *G, bool valid, int ka, int kb, int *err) {
+__device__ __forceinline__ void warp_dedup_union(int *G, bool valid, int ka, int kb, int &budget,
+                                                 int *err) {
     const unsigned long long key =
         valid ? (((unsigned long long)(uint32_t)ka << 32) | (uint32_t)kb) : ~0ull;
     const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
     const int lane = threadIdx.x & 31;
-    if (valid && (__ffs(same) - 1) == lane) gunion(G, ka, kb, err);
+    if (valid && (__ffs(same) - 1) == lane) gunion(G, ka, kb, budget, err);
 }
 
 // `idx` may lie past the last item (then the lane only takes part in the
@@ -332,6 +334,7 @@ __device__ __forceinline__ void seam_item(const ImageArgs &a, long long idx, lon
     const long long nh_real = (long long)(g.tiles_y - 1) * g.nwg;
     const long long nh = seam_h_items(g);
     int *G = a.labels;
+    int budget = kGlobHopBudget;
     if (idx < nh) {
         // horizontal seams; all 32 lanes take part in every warp-wide step
         const bool live = idx < nh_real;
@@ -382,7 +385,7 @@ __device__ __forceinline__ void seam_item(const ImageArgs &a, long long idx, lon
             }
             const bool fresh = have && !(ka == pa && kb == pb);
             if (have) { pa = ka; pb = kb; }
-            warp_dedup_union(G, fresh, ka, kb, err);
+            warp_dedup_union(G, fresh, ka, kb, budget, err);
         }
         return;
     }
@@ -417,9 +420,9 @@ __device__ __forceinline__ void seam_item(const ImageArgs &a, long long idx, lon
             kRu = __ldcg(recR + s - 1);
         }
     }
-    warp_dedup_union(G, live && (l0 | l1) && (rr0 | rr1), kL, kR, err);
-    warp_dedup_union(G, live && lu && rr0, kLu, kR, err);
-    warp_dedup_union(G, live && l0 && ru, kL, kRu, err);
+    warp_dedup_union(G, live && (l0 | l1) && (rr0 | rr1), kL, kR, budget, err);
+    warp_dedup_union(G, live && lu && rr0, kLu, kR, budget, err);
+    warp_dedup_union(G, live && l0 && ru, kL, kRu, budget, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -430,9 +433,10 @@ __device__ __forceinline__ void seam_item(const ImageArgs &a, long long idx, lon
 __device__ __forceinline__ void resolve_tile(const ImageArgs &a, int tile, int lane, int *err) {
     int *tw_ = a.tws + (size_t)tile * a.g.tile_ints;
     const int nb = min(__ldcg(tw_), a.g.border_cap);
+    int budget = kGlobHopBudget;
     for (int j = lane; j < nb; j += 32) {
         const int key = __ldcg(tw_ + a.g.off_border + j);
-        tw_[a.g.off_border + j] = 1 + gfind(a.labels, key, err);
+        tw_[a.g.off_border + j] = 1 + gfind(a.labels, key, budget, err);
     }
 }
 
