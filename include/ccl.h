@@ -100,7 +100,8 @@ ccl_status ccl_autotune(int connectivity, int reps, ccl_stream stream);
 /* Bytes of workspace ccl_label needs for this image: the largest need over
  * every tile width, so a workspace sized once stays valid if the size-class
  * table changes.  ccl_workspace_bytes_tiled: the need for one tile width
- * (tile_w 0 = the current default).  0 on invalid arguments. */
+ * (tile_w 0 = the default: same as ccl_workspace_bytes).  0 on invalid
+ * arguments. */
 size_t ccl_workspace_bytes(int height, int width, int connectivity);
 size_t ccl_workspace_bytes_tiled(int height, int width, int connectivity, int tile_w);
 

@@ -159,7 +159,7 @@ extern "C" int ccl_default_tile_width(int height, int width, int connectivity) {
 extern "C" size_t ccl_workspace_bytes_tiled(int height, int width, int connectivity,
                                             int tile_w) {
     if (!ccl::valid_image_dims(height, width) || !ccl::valid_conn(connectivity)) return 0;
-    if (tile_w == 0) tile_w = ccl::default_tile_width(height, width, connectivity);
+    if (tile_w == 0) return ccl_workspace_bytes(height, width, connectivity);
     if (!ccl::valid_tile_w(tile_w)) return 0;
     const ccl::Geom g = ccl::make_geom(height, width, connectivity, tile_w);
     return ccl::bits_bytes(g) + ccl::tiles_bytes(g);
