@@ -38,8 +38,7 @@ constexpr int kNodeCap = kThreads * 16;   // at most 16 run starts per 32-bit wo
 constexpr int kBorderCapMax = 576;        // border segments: <= 2*16*NW + 2*NS for every NW
 constexpr int kHdrInts = 4;               // [0] = border-root count
 
-constexpr int kKeyFlag = 0x40000000;      // "component touches a tile seam"
-constexpr int kKeyMask = 0x3FFFFFFF;
+constexpr int kQueueCap = 2048;           // unions left after the local forest pass
 constexpr uint32_t kEncBit = 0x80000000u; // parent pointers in the global array
 
 // device error word bits
@@ -222,16 +221,16 @@ __device__ __forceinline__ int sfind_ro(volatile const int *P, int x, int &budge
     }
 }
 
-__device__ __forceinline__ void sunion(int *P, const int *K, int a, int b, int &budget,
+__device__ __forceinline__ void sunion(int *P, const uint16_t *K, int a, int b, int &budget,
                                        int *err) {
     volatile int *vP = P;
-    volatile const int *vK = K;
+    volatile const uint16_t *vK = K;
     for (;;) {
         a = sfind(vP, a, budget, err);
         b = sfind(vP, b, budget, err);
         if (a == b) return;
         if (budget < 0) { atomicOr(err, kErrSmemUnion); return; }
-        if ((vK[a] & kKeyMask) > (vK[b] & kKeyMask)) { int t = a; a = b; b = t; }
+        if (vK[a] > vK[b]) { int t = a; a = b; b = t; }
         // link root b (larger key) under root a; fails if b stopped being a root
         if (atomicCAS(&P[b], b, a) == b) return;
     }

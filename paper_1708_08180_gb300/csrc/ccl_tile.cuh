@@ -20,14 +20,18 @@ struct ImageArgs {
 
 // Shared memory of the local-merge phase.
 struct SmemMerge {
-    int P[kNodeCap];          // parent of each segment node
-    int K[kNodeCap];          // tile-local key (min pixel index) | flags
-    uint32_t top[kThreads];   // first row of the strip, per word
-    uint32_t bot[kThreads];   // last row of the strip, per word
-    uint32_t st[kThreads];    // segment starts, per word
-    int base[kThreads];       // rank of the first segment starting in the word
+    int P[kNodeCap];               // parent of each segment node
+    uint16_t K[kNodeCap];          // key (smallest tile-local pixel index); for a
+                                   // root reaching a seam, later its border slot
+    uint32_t Q[kQueueCap];         // unions left after the forest pass: a | b << 16
+    uint32_t flag[kNodeCap / 32];  // roots whose component reaches a tile seam
+    uint32_t top[kThreads];        // first row of the strip, per word
+    uint32_t bot[kThreads];        // last row of the strip, per word
+    uint32_t st[kThreads];         // segment starts, per word
+    int base[kThreads];            // rank of the first segment starting in the word
     int warp_sums[kThreads / 32];
     int nborder;
+    int nq;
 };
 
 // Shared memory of the link phase.
@@ -85,13 +89,13 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     }
     const uint32_t top = rows[0], bot = rows[HS - 1];
     const uint32_t m = top | bot;
+    sm.top[tid] = top;
+    sm.bot[tid] = bot;
     uint32_t mL = __shfl_up_sync(0xFFFFFFFFu, m, 1);
     mL = (w > 0) ? (mL >> 31) : 0u;
     const uint32_t st = m & ~((m << 1) | mL);
     int total;
-    const int base = block_excl_scan(__popc(st), sm.warp_sums, total);
-    sm.top[tid] = top;
-    sm.bot[tid] = bot;
+    const int base = block_excl_scan(__popc(st), sm.warp_sums, total);   // syncs: top/bot visible
     sm.st[tid] = st;
     sm.base[tid] = base;
 
@@ -104,89 +108,103 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             rem &= rem - 1;
             int key;
             if (HS == 2) {
-                // length of the run from bit i to the end of this word (<= 32 - i)
+                // the run from bit i inside this word (len <= 32 - i bits)
                 const int len = __ffsll(~((unsigned long long)m >> i)) - 1;
                 const uint32_t part = (uint32_t)(((1ull << len) - 1ull) << i);
                 const uint32_t tp = top & part;
-                key = tp ? ((2 * s) * TW + 32 * w + (__ffs(tp) - 1))
-                         : ((2 * s + 1) * TW + 32 * w + i);
+                if (tp) {
+                    key = (2 * s) * TW + 32 * w + (__ffs(tp) - 1);
+                } else {
+                    // no top-row pixel here: the start's bottom pixel, unless the
+                    // segment continues and meets a top-row pixel in a later word
+                    key = (2 * s + 1) * TW + 32 * w + i;
+                    if (i + len == 32) {
+                        for (int w2 = w + 1; w2 < NW; ++w2) {
+                            const uint32_t t2 = sm.top[tid + (w2 - w)];
+                            const uint32_t m2 = t2 | sm.bot[tid + (w2 - w)];
+                            const int len2 = __ffsll(~(unsigned long long)m2) - 1;
+                            const uint32_t tp2 = t2 & (uint32_t)((1ull << len2) - 1ull);
+                            if (tp2) { key = (2 * s) * TW + 32 * w2 + (__ffs(tp2) - 1); break; }
+                            if (len2 < 32) break;
+                        }
+                    }
+                }
             } else {
                 key = s * TW + 32 * w + i;
             }
             sm.P[n] = n;
-            sm.K[n] = key;
+            sm.K[n] = (uint16_t)key;
             ++n;
         }
     }
-    if (tid == 0) sm.nborder = 0;
-    __syncthreads();
-    if (HS == 2 && (m & 1u) && !(st & 1u)) {
-        // this word continues a segment started in an earlier word; a top-row
-        // pixel here may be the segment's smallest index
-        const int len = __ffsll(~(unsigned long long)m) - 1;
-        const uint32_t part = (uint32_t)((1ull << len) - 1ull);
-        const uint32_t tp = top & part;
-        if (tp) atomicMin(&sm.K[base - 1], (2 * s) * TW + 32 * w + (__ffs(tp) - 1));
-    }
+    for (int i = tid; i < kNodeCap / 32; i += kThreads) sm.flag[i] = 0u;
+    if (tid == 0) { sm.nborder = 0; sm.nq = 0; }
     __syncthreads();
 
     // ---- a-2: union-find over the segments of the tile ----
     // Contacts join strip s-1 and strip s only.  (1) Every segment takes its
     // first contact as parent (a CAS on a segment that is still its own
     // parent): a forest whose edges all point one strip up, so each tree's
-    // root is its smallest key.  (2) Pointer jumping, in lock-step rounds,
-    // flattens that forest.  (3) The contacts are walked again and only pairs
-    // whose roots still differ are unioned (CAS link of the larger-key root
-    // under the smaller).  (4) Every node is pointed straight at its root.
-    auto contacts = [&](auto &&f) {
-        if (s == 0) return;
+    // root is its smallest key.  A contact whose CAS fails is the union of its
+    // upper segment with the parent already taken; it is queued.  (2) Pointer
+    // jumping, in lock-step rounds, flattens the forest.  (3) The queued
+    // unions are shared out evenly over the block (CAS link of the larger-key
+    // root under the smaller).  (4) Every node is pointed straight at its root.
+    int budget = kSmemHopBudget;
+    if (s > 0) {
         const int up = tid - NW;
         const uint32_t av = sm.bot[up];
         const uint32_t bv = sm.top[tid];
-        if (!bv) return;
-        const uint32_t aL = w > 0 ? (sm.bot[up - 1] >> 31) : 0u;
-        const uint32_t bL = w > 0 ? (sm.top[tid - 1] >> 31) : 0u;
-        const int baseA = sm.base[up];
-        const uint32_t stA = sm.st[up];
-        const uint32_t o = av & bv;
-        uint32_t os = o & ~((o << 1) | (aL & bL));
-        int la = -1, lb = -1;
-        auto emit = [&](int ra, int rb) {
-            if (ra != la || rb != lb) { f(ra, rb); la = ra; lb = rb; }
-        };
-        while (os) {
-            const int x = __ffs(os) - 1;
-            os &= os - 1;
-            emit(seg_rank(baseA, stA, x), seg_rank(base, st, x));
-        }
-        if (HS == 2) {
-            const uint32_t aR = w < NW - 1 ? (sm.bot[up + 1] & 1u) : 0u;
-            const uint32_t bR = w < NW - 1 ? (sm.top[tid + 1] & 1u) : 0u;
-            const uint32_t stA_next0 = w < NW - 1 ? (sm.st[up + 1] & 1u) : 0u;
-            // b-run starts at x right after an a-run that ends at x-1
-            uint32_t dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
-            // b-run ends at x right before an a-run that starts at x+1
-            uint32_t dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31));
-            while (dr) {
-                const int x = __ffs(dr) - 1;
-                dr &= dr - 1;
-                emit(seg_rank(baseA, stA, x - 1), seg_rank(base, st, x));
+        if (bv) {
+            const uint32_t aL = w > 0 ? (sm.bot[up - 1] >> 31) : 0u;
+            const uint32_t bL = w > 0 ? (sm.top[tid - 1] >> 31) : 0u;
+            const int baseA = sm.base[up];
+            const uint32_t stA = sm.st[up];
+            int la = -1, lb = -1;
+            auto contact = [&](int ra, int rb) {
+                if (ra == la && rb == lb) return;
+                la = ra;
+                lb = rb;
+                const int old = atomicCAS(&sm.P[rb], rb, ra);
+                if (old != rb && old != ra) {
+                    const int q = atomicAdd(&sm.nq, 1);
+                    if (q < kQueueCap) sm.Q[q] = (uint32_t)ra | ((uint32_t)old << 16);
+                    else sunion(sm.P, sm.K, ra, old, budget, err);   // queue full: now
+                }
+            };
+            const uint32_t o = av & bv;
+            uint32_t os = o & ~((o << 1) | (aL & bL));
+            while (os) {
+                const int x = __ffs(os) - 1;
+                os &= os - 1;
+                contact(seg_rank(baseA, stA, x), seg_rank(base, st, x));
             }
-            while (dl) {
-                const int x = __ffs(dl) - 1;
-                dl &= dl - 1;
-                emit((x == 31) ? (baseA + __popc(stA) + (int)stA_next0 - 1)
-                               : seg_rank(baseA, stA, x + 1),
-                     seg_rank(base, st, x));
+            if (HS == 2) {
+                const uint32_t aR = w < NW - 1 ? (sm.bot[up + 1] & 1u) : 0u;
+                const uint32_t bR = w < NW - 1 ? (sm.top[tid + 1] & 1u) : 0u;
+                const uint32_t stA_next0 = w < NW - 1 ? (sm.st[up + 1] & 1u) : 0u;
+                // b-run starts at x right after an a-run that ends at x-1
+                uint32_t dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
+                // b-run ends at x right before an a-run that starts at x+1
+                uint32_t dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31));
+                while (dr) {
+                    const int x = __ffs(dr) - 1;
+                    dr &= dr - 1;
+                    contact(seg_rank(baseA, stA, x - 1), seg_rank(base, st, x));
+                }
+                while (dl) {
+                    const int x = __ffs(dl) - 1;
+                    dl &= dl - 1;
+                    contact((x == 31) ? (baseA + __popc(stA) + (int)stA_next0 - 1)
+                                      : seg_rank(baseA, stA, x + 1),
+                            seg_rank(base, st, x));
+                }
             }
         }
-    };
-    volatile int *vP = sm.P;
-    int budget = kSmemHopBudget;
-    // (1) first contact becomes the parent
-    contacts([&](int ra, int rb) { atomicCAS(&sm.P[rb], rb, ra); });
+    }
     __syncthreads();
     // (2) pointer jumping until every node points at its tree's root
+    volatile int *vP = sm.P;
     for (int round = 0; round < 64; ++round) {
         int changed = 0;
         for (int n = tid; n < total; n += kThreads) {
@@ -196,11 +214,14 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         }
         if (!__syncthreads_or(changed)) break;
     }
-    // (3) the remaining joins between trees
-    contacts([&](int ra, int rb) {
-        const int pa = vP[ra], pb = vP[rb];
-        if (pa != pb) sunion(sm.P, sm.K, pa, pb, budget, err);
-    });
+    // (3) the queued unions, spread evenly over the block
+    {
+        const int nq = min(sm.nq, kQueueCap);
+        for (int i = tid; i < nq; i += kThreads) {
+            const uint32_t e = sm.Q[i];
+            sunion(sm.P, sm.K, (int)(e & 0xFFFFu), (int)(e >> 16), budget, err);
+        }
+    }
     __syncthreads();
 
     // ---- (4) roots: every node points straight at its root ----
@@ -219,6 +240,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     const bool has_left = tx > 0, has_right = tx < g.tiles_x - 1;
 
     // ---- seam records (top/bottom per column, left/right per strip) and flags ----
+    auto mark = [&](int r) { atomicOr(&sm.flag[r >> 5], 1u << (r & 31)); };
     if (tid < TW) {
         const int wc = tid >> 5, b = tid & 31;
         {   // top: strip 0
@@ -227,8 +249,8 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             int v = -1;
             if (on) {
                 const int r = sm.P[seg_rank(sm.base[o], sm.st[o], b)];
-                v = gkey(sm.K[r] & kKeyMask);
-                if (has_up && !local_only && ((sm.top[o] >> b) & 1u)) atomicOr(&sm.K[r], kKeyFlag);
+                v = gkey(sm.K[r]);
+                if (has_up && !local_only && ((sm.top[o] >> b) & 1u)) mark(r);
             }
             rec[tid] = v;
         }
@@ -238,8 +260,8 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             int v = -1;
             if (on) {
                 const int r = sm.P[seg_rank(sm.base[o], sm.st[o], b)];
-                v = gkey(sm.K[r] & kKeyMask);
-                if (has_down && !local_only && ((sm.bot[o] >> b) & 1u)) atomicOr(&sm.K[r], kKeyFlag);
+                v = gkey(sm.K[r]);
+                if (has_down && !local_only && ((sm.bot[o] >> b) & 1u)) mark(r);
             }
             rec[TW + tid] = v;
         }
@@ -250,8 +272,8 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             int v = -1;
             if ((sm.top[o] | sm.bot[o]) & 1u) {
                 const int r = sm.P[sm.base[o]];
-                v = gkey(sm.K[r] & kKeyMask);
-                if (has_left && !local_only) atomicOr(&sm.K[r], kKeyFlag);
+                v = gkey(sm.K[r]);
+                if (has_left && !local_only) mark(r);
             }
             rec[2 * TW + tid] = v;
         }
@@ -260,25 +282,25 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             int v = -1;
             if ((sm.top[o] | sm.bot[o]) >> 31) {
                 const int r = sm.P[seg_rank(sm.base[o], sm.st[o], 31)];
-                v = gkey(sm.K[r] & kKeyMask);
-                if (has_right && !local_only) atomicOr(&sm.K[r], kKeyFlag);
+                v = gkey(sm.K[r]);
+                if (has_right && !local_only) mark(r);
             }
             rec[2 * TW + NS + tid] = v;
         }
     }
     __syncthreads();
+    auto flagged = [&](int r) { return (sm.flag[r >> 5] >> (r & 31)) & 1u; };
 
     // ---- border roots: list slot + global union-find root entry ----
     if (!local_only) {
         for (int n = tid; n < total; n += kThreads) {
-            const int k = sm.K[n];
-            if (sm.P[n] == n && (k & kKeyFlag)) {
+            if (sm.P[n] == n && flagged(n)) {
                 const int j = atomicAdd(&sm.nborder, 1);
                 if (j < g.border_cap) {
-                    const int gk = gkey(k & kKeyMask);
+                    const int gk = gkey(sm.K[n]);
                     tw_[g.off_border + j] = gk;
                     a.labels[gk] = (int)((uint32_t)gk | kEncBit);
-                    sm.K[n] = kKeyFlag | j;
+                    sm.K[n] = (uint16_t)j;
                 } else {
                     atomicOr(err, kErrBorderCap);
                 }
@@ -289,8 +311,9 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
 
     // ---- per-segment labels ----
     for (int n = tid; n < total; n += kThreads) {
-        const int k = sm.K[sm.P[n]];
-        tw_[kHdrInts + n] = (k & kKeyFlag) ? -(1 + (k & kKeyMask)) : 1 + gkey(k & kKeyMask);
+        const int r = sm.P[n];
+        const int k = sm.K[r];
+        tw_[kHdrInts + n] = flagged(r) ? -(1 + k) : 1 + gkey(k);
     }
     if (tid == 0) tw_[0] = local_only ? 0 : min(sm.nborder, g.border_cap);
 }
