@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kThreads) kb_merge(BatchHeader *hdr, const Bat
 
 __global__ void __launch_bounds__(256) kb_seams(BatchHeader *hdr, const BatchImage *imgs,
                                                 int *err) {
+    __shared__ SmemSeams sm;
     __shared__ long long s_chunk;
     __shared__ int s_img;
     const int n = hdr->n;
@@ -103,8 +104,7 @@ __global__ void __launch_bounds__(256) kb_seams(BatchHeader *hdr, const BatchIma
         const long long c = s_chunk;
         if (c >= total) break;
         const ImageArgs a = imgs[s_img].a;
-        const long long item = (c - imgs[s_img].chunk_off) * 256 + threadIdx.x;
-        seam_item(a, item, seam_items(a.g), err);   // every lane takes part
+        seam_block(a, (c - imgs[s_img].chunk_off) * 256, seam_items(a.g), sm, err);
         __syncthreads();
     }
 }

@@ -15,8 +15,8 @@ __global__ void __launch_bounds__(kThreads) k_merge(ImageArgs a, int local_only,
 }
 
 __global__ void __launch_bounds__(256) k_seams(ImageArgs a, long long nitems, int *err) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    seam_item(a, idx, nitems, err);   // every lane takes part (warp-wide dedup)
+    __shared__ SmemSeams sm;
+    seam_block(a, (long long)blockIdx.x * 256, nitems, sm, err);
 }
 
 // one warp per tile: final labels of the tile's border roots

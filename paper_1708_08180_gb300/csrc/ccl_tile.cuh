@@ -323,9 +323,8 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
 // words (rows y-1, y with y = ty*TH), (tiles_y-1)*nwg of them, padded to a
 // multiple of 256 so that no warp or 256-item chunk mixes the two kinds; then
 // one item per strip of each vertical seam, (tiles_x-1)*tiles_y*NS.  Each
-// touching pair of runs across a seam yields one union of the two local roots;
-// a warp (32 consecutive words or strips of one seam) drops equal pairs first,
-// which are the rule when one component crosses the seam many times.
+// touching pair of runs across a seam yields one union of the two local roots
+// (deduplicated per block of 256 items, see seam_block).
 __device__ __forceinline__ uint32_t bit_at(const uint32_t *bits, int nwg, int y, int x) {
     return (__ldcg(bits + (size_t)y * nwg + (x >> 5)) >> (x & 31)) & 1u;
 }
@@ -338,114 +337,119 @@ __host__ __device__ inline long long seam_items(const Geom &g) {
     return seam_h_items(g) + (long long)(g.tiles_x - 1) * g.tiles_y * g.ns;
 }
 
-// union (ka, kb) unless another lane of the warp holds the same pair and a
-// lower lane id; all 32 lanes must call it (valid = false to abstain)
-__device__ __forceinline__ void warp_dedup_union(int *G, bool valid, int ka, int kb, int &budget,
-                                                 int *err) {
-    const unsigned long long key =
-        valid ? (((unsigned long long)(uint32_t)ka << 32) | (uint32_t)kb) : ~0ull;
-    const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
-    const int lane = threadIdx.x & 31;
-    if (valid && (__ffs(same) - 1) == lane) gunion(G, ka, kb, budget, err);
+// Seam unions of one block of 256 items.  Every item first offers its pairs
+// (local root above/left, local root below/right) to a block-wide hash set in
+// shared memory, which keeps one copy of each pair (one component crossing a
+// seam many times yields the same pair over and over); then the threads run
+// the surviving unions in parallel, so a block costs about one union's chain
+// of dependent global loads instead of one per contact.
+constexpr int kSeamSlots = 512;
+constexpr unsigned long long kSeamEmpty = ~0ull;
+
+struct SmemSeams {
+    unsigned long long slot[kSeamSlots];
+};
+
+__device__ __forceinline__ void seam_offer(SmemSeams &sm, int *G, int ka, int kb, int &budget,
+                                           int *err) {
+    const unsigned long long key = ((unsigned long long)(uint32_t)ka << 32) | (uint32_t)kb;
+    uint32_t h = ((uint32_t)ka * 0x9E3779B1u) ^ ((uint32_t)kb * 0x85EBCA77u);
+    h = (h ^ (h >> 15)) & (kSeamSlots - 1);
+    for (int probe = 0; probe < kSeamSlots; ++probe) {
+        const unsigned long long old = atomicCAS(&sm.slot[h], kSeamEmpty, key);
+        if (old == kSeamEmpty || old == key) return;   // stored, or already there
+        h = (h + 1) & (kSeamSlots - 1);
+    }
+    gunion(G, ka, kb, budget, err);   // set full: union right away
 }
 
-// `idx` may lie past the last item (then the lane only takes part in the
-// warp-wide steps); items of one warp are all horizontal or all vertical.
-__device__ __forceinline__ void seam_item(const ImageArgs &a, long long idx, long long nitems,
-                                          int *err) {
+// Pairs of item `idx` (horizontal: one 32-pixel word of a seam row pair;
+// vertical: one strip of a vertical seam); idx may lie past the last item.
+__device__ __forceinline__ void seam_item_offer(const ImageArgs &a, long long idx,
+                                                long long nitems, SmemSeams &sm, int &budget,
+                                                int *err) {
     const Geom &g = a.g;
     const long long nh_real = (long long)(g.tiles_y - 1) * g.nwg;
     const long long nh = seam_h_items(g);
     int *G = a.labels;
-    int budget = kGlobHopBudget;
     if (idx < nh) {
-        // horizontal seams; all 32 lanes take part in every warp-wide step
-        const bool live = idx < nh_real;
-        const int ty = live ? (int)(idx / g.nwg) + 1 : 1;
-        const int j = live ? (int)(idx % g.nwg) : 0;
-        uint32_t os = 0, dr = 0, dl = 0;
-        const int *tbase_up = nullptr, *tbase_dn = nullptr;
-        if (live) {
-            const int y = ty * g.th;
-            const uint32_t *ra_ = a.bits + (size_t)(y - 1) * g.nwg;
-            const uint32_t *rb_ = a.bits + (size_t)y * g.nwg;
-            const uint32_t av = __ldcg(ra_ + j), bv = __ldcg(rb_ + j);
-            if (bv) {   // every contact needs a pixel in row y
-                const uint32_t aL = j > 0 ? (__ldcg(ra_ + j - 1) >> 31) : 0u;
-                const uint32_t bL = j > 0 ? (__ldcg(rb_ + j - 1) >> 31) : 0u;
-                const uint32_t aR = j < g.nwg - 1 ? (__ldcg(ra_ + j + 1) & 1u) : 0u;
-                const uint32_t bR = j < g.nwg - 1 ? (__ldcg(rb_ + j + 1) & 1u) : 0u;
-                const uint32_t o = av & bv;
-                os = o & ~((o << 1) | (aL & bL));
-                if (g.hs == 2) {
-                    dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
-                    dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31));
-                }
-            }
-            tbase_up = a.tws + (size_t)(ty - 1) * g.tiles_x * g.tile_ints + g.off_rec + g.tw;
-            tbase_dn = a.tws + (size_t)ty * g.tiles_x * g.tile_ints + g.off_rec;
-        }
+        if (idx >= nh_real) return;
+        const int ty = (int)(idx / g.nwg) + 1;
+        const int j = (int)(idx % g.nwg);
+        const int y = ty * g.th;
+        const uint32_t *ra_ = a.bits + (size_t)(y - 1) * g.nwg;
+        const uint32_t *rb_ = a.bits + (size_t)y * g.nwg;
+        const uint32_t av = __ldcg(ra_ + j), bv = __ldcg(rb_ + j);
+        if (!bv) return;   // every contact needs a pixel in row y
+        const uint32_t aL = j > 0 ? (__ldcg(ra_ + j - 1) >> 31) : 0u;
+        const uint32_t bL = j > 0 ? (__ldcg(rb_ + j - 1) >> 31) : 0u;
+        const uint32_t aR = j < g.nwg - 1 ? (__ldcg(ra_ + j + 1) & 1u) : 0u;
+        const uint32_t bR = j < g.nwg - 1 ? (__ldcg(rb_ + j + 1) & 1u) : 0u;
+        const int *tbase_up = a.tws + (size_t)(ty - 1) * g.tiles_x * g.tile_ints + g.off_rec + g.tw;
+        const int *tbase_dn = a.tws + (size_t)ty * g.tiles_x * g.tile_ints + g.off_rec;
         auto rec_up = [&](int xg) { return __ldcg(tbase_up + (size_t)(xg >> g.log2tw) * g.tile_ints + (xg & (g.tw - 1))); };
         auto rec_dn = [&](int xg) { return __ldcg(tbase_dn + (size_t)(xg >> g.log2tw) * g.tile_ints + (xg & (g.tw - 1))); };
-        const int xw = 32 * j;
         int pa = -1, pb = -1;
-        // one contact per lane per round; equal pairs across the warp (one
-        // component crossing the seam many times) are unioned by one lane
-        while (__any_sync(0xFFFFFFFFu, (os | dr | dl) != 0u)) {
-            int ka = -1, kb = -1;
-            bool have = true;
-            if (os) {
-                const int x = __ffs(os) - 1; os &= os - 1;
-                ka = rec_up(xw + x); kb = rec_dn(xw + x);
-            } else if (dr) {
-                const int x = __ffs(dr) - 1; dr &= dr - 1;
-                ka = rec_up(xw + x - 1); kb = rec_dn(xw + x);
-            } else if (dl) {
-                const int x = __ffs(dl) - 1; dl &= dl - 1;
-                ka = rec_up(xw + x + 1); kb = rec_dn(xw + x);
-            } else {
-                have = false;
-            }
-            const bool fresh = have && !(ka == pa && kb == pb);
-            if (have) { pa = ka; pb = kb; }
-            warp_dedup_union(G, fresh, ka, kb, budget, err);
+        auto contact = [&](int xa, int xb) {
+            const int ka = rec_up(xa), kb = rec_dn(xb);
+            if (ka == pa && kb == pb) return;
+            pa = ka;
+            pb = kb;
+            seam_offer(sm, G, ka, kb, budget, err);
+        };
+        const uint32_t o = av & bv;
+        uint32_t os = o & ~((o << 1) | (aL & bL));
+        const int xw = 32 * j;
+        while (os) { const int x = __ffs(os) - 1; os &= os - 1; contact(xw + x, xw + x); }
+        if (g.hs == 2) {
+            uint32_t dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
+            uint32_t dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31));
+            while (dr) { const int x = __ffs(dr) - 1; dr &= dr - 1; contact(xw + x - 1, xw + x); }
+            while (dl) { const int x = __ffs(dl) - 1; dl &= dl - 1; contact(xw + x + 1, xw + x); }
         }
         return;
     }
-    // vertical seams: every lane reaches the three warp-wide dedup steps
+    if (idx >= nitems) return;
     const long long v = idx - nh;
-    bool live = idx < nitems;
     const int s = (int)(v % g.ns);
     const long long t = v / g.ns;
     const int ty = (int)(t % g.tiles_y);
     const int tx = (int)(t / g.tiles_y) + 1;
     const int x = tx * g.tw;
     const int r0 = ty * g.th + s * g.hs;
-    live = live && r0 < g.H;
-    int kL = -1, kR = -1, kLu = -1, kRu = -1;
-    uint32_t l0 = 0, l1 = 0, rr0 = 0, rr1 = 0, lu = 0, ru = 0;
-    if (live) {
-        const int *recL = a.tws + ((size_t)ty * g.tiles_x + (tx - 1)) * g.tile_ints + g.off_rec + 2 * g.tw + g.ns;
-        const int *recR = a.tws + ((size_t)ty * g.tiles_x + tx) * g.tile_ints + g.off_rec + 2 * g.tw;
-        l0 = bit_at(a.bits, g.nwg, r0, x - 1);
-        rr0 = bit_at(a.bits, g.nwg, r0, x);
-        if (g.hs == 2 && r0 + 1 < g.H) {
-            l1 = bit_at(a.bits, g.nwg, r0 + 1, x - 1);
-            rr1 = bit_at(a.bits, g.nwg, r0 + 1, x);
-        }
-        kL = __ldcg(recL + s);
-        kR = __ldcg(recR + s);
-        if (g.hs == 2 && s > 0) {
-            // diagonals between the last row of strip s-1 and the first of strip s
-            lu = bit_at(a.bits, g.nwg, r0 - 1, x - 1);
-            ru = bit_at(a.bits, g.nwg, r0 - 1, x);
-            kLu = __ldcg(recL + s - 1);
-            kRu = __ldcg(recR + s - 1);
-        }
+    if (r0 >= g.H) return;
+    const int *recL = a.tws + ((size_t)ty * g.tiles_x + (tx - 1)) * g.tile_ints + g.off_rec + 2 * g.tw + g.ns;
+    const int *recR = a.tws + ((size_t)ty * g.tiles_x + tx) * g.tile_ints + g.off_rec + 2 * g.tw;
+    const uint32_t l0 = bit_at(a.bits, g.nwg, r0, x - 1);
+    const uint32_t rr0 = bit_at(a.bits, g.nwg, r0, x);
+    uint32_t l1 = 0, rr1 = 0;
+    if (g.hs == 2 && r0 + 1 < g.H) {
+        l1 = bit_at(a.bits, g.nwg, r0 + 1, x - 1);
+        rr1 = bit_at(a.bits, g.nwg, r0 + 1, x);
     }
-    warp_dedup_union(G, live && (l0 | l1) && (rr0 | rr1), kL, kR, budget, err);
-    warp_dedup_union(G, live && lu && rr0, kLu, kR, budget, err);
-    warp_dedup_union(G, live && l0 && ru, kL, kRu, budget, err);
+    if ((l0 | l1) && (rr0 | rr1)) seam_offer(sm, G, __ldcg(recL + s), __ldcg(recR + s), budget, err);
+    if (g.hs == 2 && s > 0) {
+        // diagonals between the last row of strip s-1 and the first of strip s
+        const uint32_t lu = bit_at(a.bits, g.nwg, r0 - 1, x - 1);
+        const uint32_t ru = bit_at(a.bits, g.nwg, r0 - 1, x);
+        if (lu && rr0) seam_offer(sm, G, __ldcg(recL + s - 1), __ldcg(recR + s), budget, err);
+        if (l0 && ru) seam_offer(sm, G, __ldcg(recL + s), __ldcg(recR + s - 1), budget, err);
+    }
+}
+
+// One block of 256 seam items (block-uniform call: contains barriers).
+__device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, long long nitems,
+                                           SmemSeams &sm, int *err) {
+    for (int i = threadIdx.x; i < kSeamSlots; i += blockDim.x) sm.slot[i] = kSeamEmpty;
+    __syncthreads();
+    int budget = kGlobHopBudget;
+    seam_item_offer(a, idx0 + threadIdx.x, nitems, sm, budget, err);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSeamSlots; i += blockDim.x) {
+        const unsigned long long key = sm.slot[i];
+        if (key != kSeamEmpty)
+            gunion(a.labels, (int)(uint32_t)(key >> 32), (int)(uint32_t)key, budget, err);
+    }
 }
 
 // ---------------------------------------------------------------------------
