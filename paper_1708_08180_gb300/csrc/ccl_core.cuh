@@ -39,6 +39,7 @@ constexpr int kBorderCapMax = 576;        // border segments: <= 2*16*NW + 2*NS 
 constexpr int kHdrInts = 4;               // [0] = border-root count
 
 constexpr int kQueueCap = 2048;           // unions left after the local forest pass
+constexpr uint32_t kQueueEmpty = 0xFFFFFFFFu;
 constexpr uint32_t kEncBit = 0x80000000u; // parent pointers in the global array
 
 // device error word bits

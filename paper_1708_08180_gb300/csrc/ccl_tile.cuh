@@ -23,7 +23,8 @@ struct SmemMerge {
     int P[kNodeCap];               // parent of each segment node
     uint16_t K[kNodeCap];          // key (smallest tile-local pixel index); for a
                                    // root reaching a seam, later its border slot
-    uint32_t Q[kQueueCap];         // unions left after the forest pass: a | b << 16
+    uint32_t Q[kQueueCap];         // unions left after the forest pass: a | b << 16;
+                                   // thread t owns slots t, t + 256, ... (no atomics)
     uint32_t flag[kNodeCap / 32];  // roots whose component reaches a tile seam
     uint32_t top[kThreads];        // first row of the strip, per word
     uint32_t bot[kThreads];        // last row of the strip, per word
@@ -31,7 +32,6 @@ struct SmemMerge {
     int base[kThreads];            // rank of the first segment starting in the word
     int warp_sums[kThreads / 32];
     int nborder;
-    int nq;
 };
 
 // Shared memory of the link phase.
@@ -138,7 +138,8 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         }
     }
     for (int i = tid; i < kNodeCap / 32; i += kThreads) sm.flag[i] = 0u;
-    if (tid == 0) { sm.nborder = 0; sm.nq = 0; }
+    for (int i = tid; i < kQueueCap; i += kThreads) sm.Q[i] = kQueueEmpty;
+    if (tid == 0) sm.nborder = 0;
     __syncthreads();
 
     // ---- a-2: union-find over the segments of the tile ----
@@ -151,6 +152,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     // unions are shared out evenly over the block (CAS link of the larger-key
     // root under the smaller).  (4) Every node is pointed straight at its root.
     int budget = kSmemHopBudget;
+    int nq = 0;   // this thread's queued unions (slots tid + 256 * k)
     if (s > 0) {
         const int up = tid - NW;
         const uint32_t av = sm.bot[up];
@@ -167,9 +169,10 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
                 lb = rb;
                 const int old = atomicCAS(&sm.P[rb], rb, ra);
                 if (old != rb && old != ra) {
-                    const int q = atomicAdd(&sm.nq, 1);
-                    if (q < kQueueCap) sm.Q[q] = (uint32_t)ra | ((uint32_t)old << 16);
-                    else sunion(sm.P, sm.K, ra, old, budget, err);   // queue full: now
+                    if (nq < kQueueCap / kThreads)
+                        sm.Q[(nq++) * kThreads + tid] = (uint32_t)ra | ((uint32_t)old << 16);
+                    else
+                        sunion(sm.P, sm.K, ra, old, budget, err);   // slots full: now
                 }
             };
             const uint32_t o = av & bv;
@@ -215,12 +218,9 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         if (!__syncthreads_or(changed)) break;
     }
     // (3) the queued unions, spread evenly over the block
-    {
-        const int nq = min(sm.nq, kQueueCap);
-        for (int i = tid; i < nq; i += kThreads) {
-            const uint32_t e = sm.Q[i];
-            sunion(sm.P, sm.K, (int)(e & 0xFFFFu), (int)(e >> 16), budget, err);
-        }
+    for (int i = tid; i < kQueueCap; i += kThreads) {
+        const uint32_t e = sm.Q[i];
+        if (e != kQueueEmpty) sunion(sm.P, sm.K, (int)(e & 0xFFFFu), (int)(e >> 16), budget, err);
     }
     __syncthreads();
 
@@ -337,41 +337,70 @@ __host__ __device__ inline long long seam_items(const Geom &g) {
     return seam_h_items(g) + (long long)(g.tiles_x - 1) * g.tiles_y * g.ns;
 }
 
-// Seam unions of one block of 256 items.  Every item first offers its pairs
-// (local root above/left, local root below/right) to a block-wide hash set in
-// shared memory, which keeps one copy of each pair (one component crossing a
-// seam many times yields the same pair over and over); then the threads run
-// the surviving unions in parallel, so a block costs about one union's chain
-// of dependent global loads instead of one per contact.
-constexpr int kSeamSlots = 512;
-constexpr unsigned long long kSeamEmpty = ~0ull;
+// Seam unions of one block of 256 items, warp by warp.  Each round every lane
+// offers its next pair (local root above/left, local root below/right); lanes
+// holding equal pairs elect one leader (__match_any_sync), and leaders append
+// their pair to the warp's list (slots from a ballot, no atomics).  One
+// component crossing a seam many times yields the same pair over and over, so
+// the lists stay short.  Then the warp's lanes run the listed unions in
+// parallel: a warp costs about one union's chain of dependent global loads
+// instead of one per contact.
+constexpr int kSeamList = 128;   // pairs per warp before falling back to direct unions
 
 struct SmemSeams {
-    unsigned long long slot[kSeamSlots];
+    int2 list[kThreads / 32][kSeamList];
 };
 
-__device__ __forceinline__ void seam_offer(SmemSeams &sm, int *G, int ka, int kb, int &budget,
-                                           int *err) {
-    const unsigned long long key = ((unsigned long long)(uint32_t)ka << 32) | (uint32_t)kb;
-    uint32_t h = ((uint32_t)ka * 0x9E3779B1u) ^ ((uint32_t)kb * 0x85EBCA77u);
-    h = (h ^ (h >> 15)) & (kSeamSlots - 1);
-    for (int probe = 0; probe < kSeamSlots; ++probe) {
-        const unsigned long long old = atomicCAS(&sm.slot[h], kSeamEmpty, key);
-        if (old == kSeamEmpty || old == key) return;   // stored, or already there
-        h = (h + 1) & (kSeamSlots - 1);
-    }
-    gunion(G, ka, kb, budget, err);   // set full: union right away
-}
+// Per-lane pair generator for item `idx` (horizontal: one 32-pixel word of a
+// seam row pair; vertical: one strip of a vertical seam).  next() yields the
+// item's pairs one at a time (consecutive repeats dropped) and false when done.
+struct SeamPairs {
+    // horizontal state
+    uint32_t os = 0, dr = 0, dl = 0;
+    int xw = 0;
+    const int *up = nullptr, *dn = nullptr;
+    int tile_ints = 0, log2tw = 0, twm = 0;
+    // vertical state: up to three candidate pairs
+    int nv = 0, vi = 0;
+    int va0 = -1, vb0 = -1, va1 = -1, vb1 = -1, va2 = -1, vb2 = -1;
+    int la = -1, lb = -1;
 
-// Pairs of item `idx` (horizontal: one 32-pixel word of a seam row pair;
-// vertical: one strip of a vertical seam); idx may lie past the last item.
-__device__ __forceinline__ void seam_item_offer(const ImageArgs &a, long long idx,
-                                                long long nitems, SmemSeams &sm, int &budget,
-                                                int *err) {
+    __device__ __forceinline__ void push(int ka, int kb) {
+        if (nv == 0) { va0 = ka; vb0 = kb; } else if (nv == 1) { va1 = ka; vb1 = kb; } else { va2 = ka; vb2 = kb; }
+        ++nv;
+    }
+
+    __device__ __forceinline__ int rec(const int *b, int xg) const {
+        return __ldcg(b + (size_t)(xg >> log2tw) * tile_ints + (xg & twm));
+    }
+    __device__ __forceinline__ bool next(int &ka, int &kb) {
+        for (;;) {
+            if (os) {
+                const int x = __ffs(os) - 1; os &= os - 1;
+                ka = rec(up, xw + x); kb = rec(dn, xw + x);
+            } else if (dr) {
+                const int x = __ffs(dr) - 1; dr &= dr - 1;
+                ka = rec(up, xw + x - 1); kb = rec(dn, xw + x);
+            } else if (dl) {
+                const int x = __ffs(dl) - 1; dl &= dl - 1;
+                ka = rec(up, xw + x + 1); kb = rec(dn, xw + x);
+            } else if (vi < nv) {
+                ka = vi == 0 ? va0 : vi == 1 ? va1 : va2;
+                kb = vi == 0 ? vb0 : vi == 1 ? vb1 : vb2;
+                ++vi;
+            } else {
+                return false;
+            }
+            if (ka != la || kb != lb) { la = ka; lb = kb; return true; }
+        }
+    }
+};
+
+__device__ __forceinline__ void seam_pairs_init(const ImageArgs &a, long long idx,
+                                                long long nitems, SeamPairs &sp) {
     const Geom &g = a.g;
     const long long nh_real = (long long)(g.tiles_y - 1) * g.nwg;
     const long long nh = seam_h_items(g);
-    int *G = a.labels;
     if (idx < nh) {
         if (idx >= nh_real) return;
         const int ty = (int)(idx / g.nwg) + 1;
@@ -385,27 +414,17 @@ __device__ __forceinline__ void seam_item_offer(const ImageArgs &a, long long id
         const uint32_t bL = j > 0 ? (__ldcg(rb_ + j - 1) >> 31) : 0u;
         const uint32_t aR = j < g.nwg - 1 ? (__ldcg(ra_ + j + 1) & 1u) : 0u;
         const uint32_t bR = j < g.nwg - 1 ? (__ldcg(rb_ + j + 1) & 1u) : 0u;
-        const int *tbase_up = a.tws + (size_t)(ty - 1) * g.tiles_x * g.tile_ints + g.off_rec + g.tw;
-        const int *tbase_dn = a.tws + (size_t)ty * g.tiles_x * g.tile_ints + g.off_rec;
-        auto rec_up = [&](int xg) { return __ldcg(tbase_up + (size_t)(xg >> g.log2tw) * g.tile_ints + (xg & (g.tw - 1))); };
-        auto rec_dn = [&](int xg) { return __ldcg(tbase_dn + (size_t)(xg >> g.log2tw) * g.tile_ints + (xg & (g.tw - 1))); };
-        int pa = -1, pb = -1;
-        auto contact = [&](int xa, int xb) {
-            const int ka = rec_up(xa), kb = rec_dn(xb);
-            if (ka == pa && kb == pb) return;
-            pa = ka;
-            pb = kb;
-            seam_offer(sm, G, ka, kb, budget, err);
-        };
+        sp.up = a.tws + (size_t)(ty - 1) * g.tiles_x * g.tile_ints + g.off_rec + g.tw;
+        sp.dn = a.tws + (size_t)ty * g.tiles_x * g.tile_ints + g.off_rec;
+        sp.tile_ints = g.tile_ints;
+        sp.log2tw = g.log2tw;
+        sp.twm = g.tw - 1;
+        sp.xw = 32 * j;
         const uint32_t o = av & bv;
-        uint32_t os = o & ~((o << 1) | (aL & bL));
-        const int xw = 32 * j;
-        while (os) { const int x = __ffs(os) - 1; os &= os - 1; contact(xw + x, xw + x); }
+        sp.os = o & ~((o << 1) | (aL & bL));
         if (g.hs == 2) {
-            uint32_t dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
-            uint32_t dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31));
-            while (dr) { const int x = __ffs(dr) - 1; dr &= dr - 1; contact(xw + x - 1, xw + x); }
-            while (dl) { const int x = __ffs(dl) - 1; dl &= dl - 1; contact(xw + x + 1, xw + x); }
+            sp.dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
+            sp.dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31));
         }
         return;
     }
@@ -427,29 +446,44 @@ __device__ __forceinline__ void seam_item_offer(const ImageArgs &a, long long id
         l1 = bit_at(a.bits, g.nwg, r0 + 1, x - 1);
         rr1 = bit_at(a.bits, g.nwg, r0 + 1, x);
     }
-    if ((l0 | l1) && (rr0 | rr1)) seam_offer(sm, G, __ldcg(recL + s), __ldcg(recR + s), budget, err);
+    if ((l0 | l1) && (rr0 | rr1)) sp.push(__ldcg(recL + s), __ldcg(recR + s));
     if (g.hs == 2 && s > 0) {
         // diagonals between the last row of strip s-1 and the first of strip s
         const uint32_t lu = bit_at(a.bits, g.nwg, r0 - 1, x - 1);
         const uint32_t ru = bit_at(a.bits, g.nwg, r0 - 1, x);
-        if (lu && rr0) seam_offer(sm, G, __ldcg(recL + s - 1), __ldcg(recR + s), budget, err);
-        if (l0 && ru) seam_offer(sm, G, __ldcg(recL + s), __ldcg(recR + s - 1), budget, err);
+        if (lu && rr0) sp.push(__ldcg(recL + s - 1), __ldcg(recR + s));
+        if (l0 && ru) sp.push(__ldcg(recL + s), __ldcg(recR + s - 1));
     }
 }
 
-// One block of 256 seam items (block-uniform call: contains barriers).
+// One block of 256 seam items; every lane of every warp must call it.
 __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, long long nitems,
                                            SmemSeams &sm, int *err) {
-    for (int i = threadIdx.x; i < kSeamSlots; i += blockDim.x) sm.slot[i] = kSeamEmpty;
-    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int budget = kGlobHopBudget;
-    seam_item_offer(a, idx0 + threadIdx.x, nitems, sm, budget, err);
-    __syncthreads();
-    for (int i = threadIdx.x; i < kSeamSlots; i += blockDim.x) {
-        const unsigned long long key = sm.slot[i];
-        if (key != kSeamEmpty)
-            gunion(a.labels, (int)(uint32_t)(key >> 32), (int)(uint32_t)key, budget, err);
+    SeamPairs sp;
+    seam_pairs_init(a, idx0 + threadIdx.x, nitems, sp);
+    int2 *list = sm.list[warp];
+    int n = 0;   // warp-uniform list length
+    for (;;) {
+        int ka = -1, kb = -1;
+        const bool have = sp.next(ka, kb);
+        if (!__any_sync(0xFFFFFFFFu, have)) break;
+        const unsigned long long key =
+            have ? (((unsigned long long)(uint32_t)ka << 32) | (uint32_t)kb) : ~0ull;
+        const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
+        const bool leader = have && (__ffs(same) - 1) == lane;
+        const unsigned lead = __ballot_sync(0xFFFFFFFFu, leader);
+        if (leader) {
+            const int slot = n + __popc(lead & ((1u << lane) - 1u));
+            if (slot < kSeamList) list[slot] = make_int2(ka, kb);
+            else gunion(a.labels, ka, kb, budget, err);   // list full: union now
+        }
+        n += __popc(lead);
     }
+    __syncwarp();
+    const int m = n < kSeamList ? n : kSeamList;
+    for (int i = lane; i < m; i += 32) gunion(a.labels, list[i].x, list[i].y, budget, err);
 }
 
 // ---------------------------------------------------------------------------
