@@ -39,8 +39,7 @@ constexpr int kBorderCapMax = 576;        // border segments: <= 2*16*NW + 2*NS 
 constexpr int kHdrInts = 4;               // [0] = border-root count
 
 constexpr int kQueueCap = 2048;           // unions left after the local forest pass
-constexpr uint32_t kQueueEmpty = 0xFFFFFFFFu;
-constexpr uint32_t kEncBit = 0x80000000u; // parent pointers in the global array
+constexpr int kSlotBits = 10;             // global node = tile << kSlotBits | border slot
 
 // device error word bits
 constexpr int kErrSmemFind = 1;
@@ -60,10 +59,16 @@ constexpr int kGlobHopBudget = 1 << 20;   // per thread per work item (global me
 
 // Geometry of one image under one tile shape, and the layout of the per-tile
 // workspace (all offsets in ints from the tile's base):
-//   [0, kHdrInts)                header: [0] = number of border roots
-//   [kHdrInts, off_border)       label of each segment node (node_cap)
-//   [off_border, off_rec)        global index of each border root (border_cap)
-//   [off_rec, off_rec + rec)     seam records: top[tw], bottom[tw], left[ns], right[ns]
+//   [0, kHdrInts)               header: [0] = number of border roots
+//   [kHdrInts, off_key)         label of each segment node (node_cap)
+//   [off_key, off_min)          smallest raster index of each border root's component
+//                               inside the tile (border_cap)
+//   [off_min, off_par)          smallest raster index of its global set, valid at a
+//                               global root once the resolve pass has run (border_cap)
+//   [off_par, off_rec)          parent of each border root in the global forest,
+//                               64-bit node ids (border_cap x 2 ints, 8-byte aligned)
+//   [off_rec, off_rec + rec)    seam records, border slot of the root (-1: none):
+//                               top[tw], bottom[tw], left[ns], right[ns]
 struct Geom {
     int H, W;
     int nw;         // 32-bit words per tile row: 1, 2, 4, 8
@@ -75,7 +80,7 @@ struct Geom {
     int nwg;        // words per bit-image row = ceil(W / 32)
     int node_cap;   // most segment nodes a tile of this image can hold
     int border_cap; // most border roots
-    int off_border, off_rec, tile_ints;
+    int off_key, off_min, off_par, off_rec, tile_ints;
 };
 
 __host__ __device__ inline Geom make_geom(int H, int W, int conn, int tile_w) {
@@ -96,8 +101,10 @@ __host__ __device__ inline Geom make_geom(int H, int W, int conn, int tile_w) {
     const int per_strip = (cols + 1) / 2;
     g.node_cap = g.ns * per_strip;
     g.border_cap = 2 * per_strip + 2 * g.ns;
-    g.off_border = kHdrInts + g.node_cap;
-    g.off_rec = g.off_border + g.border_cap;
+    g.off_key = kHdrInts + g.node_cap;
+    g.off_min = g.off_key + g.border_cap;
+    g.off_par = (g.off_min + g.border_cap + 1) & ~1;
+    g.off_rec = g.off_par + 2 * g.border_cap;
     g.tile_ints = (g.off_rec + 2 * g.tw + 2 * g.ns + 63) & ~63;   // 256-byte multiple
     return g;
 }
@@ -238,45 +245,70 @@ __device__ __forceinline__ void sunion(int *P, const uint16_t *K, int a, int b, 
 }
 
 // ---------------------------------------------------------------------------
-// union-find in global memory over raster indices (keys), stored in the label
-// buffer itself: G[x] = x | kEncBit is a parent pointer (negative as int32),
-// a value >= 0 is a final label (only written by the link phase).
+// union-find in global memory over the border roots of all tiles.  A node is
+// (tile << kSlotBits | slot), 64-bit; its parent lives in the owning tile's
+// workspace.  Roots are linked by a fixed pseudo-random priority of the node
+// id (randomised linking keeps the forest shallow when thousands of tiles
+// merge at once, where "link to the smaller index" builds long chains); the
+// smallest raster index of each set is gathered separately (resolve pass).
 
-__device__ __forceinline__ int gload(const int *p) { return __ldcg(p); }
+typedef unsigned long long gnode;
+constexpr gnode kNoNode = ~0ull;
 
-__device__ __forceinline__ int gfind(int *G, int x, int &budget, int *err) {
+__device__ __forceinline__ gnode make_gnode(long long tile, int slot) {
+    return ((gnode)tile << kSlotBits) | (gnode)slot;
+}
+
+// priority: a bijective 64-bit mix (SplitMix64 finaliser, Steele et al. 2014)
+__device__ __forceinline__ unsigned long long gprio(gnode x) {
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+struct GlobalForest {
+    int *tws;
+    int tile_ints, off_par;
+    __device__ __forceinline__ gnode *par(gnode n) const {
+        return reinterpret_cast<gnode *>(tws + (size_t)(n >> kSlotBits) * tile_ints + off_par) +
+               (n & ((1u << kSlotBits) - 1u));
+    }
+};
+
+__device__ __forceinline__ gnode gfind(const GlobalForest &F, gnode x, int &budget, int *err) {
     // walk to the root r ...
-    int r = x;
+    gnode r = x;
     for (;;) {
         if (--budget < 0) { atomicOr(err, kErrGlobFind); return r; }
-        const int p = (int)((uint32_t)gload(G + r) & ~kEncBit);
+        const gnode p = __ldcg(F.par(r));
         if (p == r) break;
         r = p;
     }
-    // ... then point the walked nodes at r.  Parents always have smaller
-    // indices, so only nodes above r in index (x > r) are rewritten: a path
-    // that another thread has meanwhile compressed past r is left alone
-    // instead of being pointed back down (which would close a cycle).
-    const int er = (int)((uint32_t)r | kEncBit);
-    while (x > r) {
+    // ... then point the walked nodes at r.  Priorities strictly increase
+    // along parent links, so only nodes below r (lower priority) are
+    // rewritten: a path another thread has meanwhile compressed past r is left
+    // alone instead of being pointed back down (which would close a cycle).
+    const unsigned long long pr = gprio(r);
+    while (x != r) {
         if (--budget < 0) { atomicOr(err, kErrGlobFind); return r; }
-        const int p = (int)((uint32_t)gload(G + x) & ~kEncBit);
-        if (p <= r) break;
-        __stcg(G + x, er);   // x is not a root: no link can target it
+        const gnode p = __ldcg(F.par(x));
+        if (p == r || gprio(p) >= pr) break;
+        __stcg(F.par(x), r);   // x is not a root: no link can target it
         x = p;
     }
     return r;
 }
 
-__device__ __forceinline__ void gunion(int *G, int a, int b, int &budget, int *err) {
+__device__ __forceinline__ void gunion(const GlobalForest &F, gnode a, gnode b, int &budget,
+                                       int *err) {
     for (;;) {
-        a = gfind(G, a, budget, err);
-        b = gfind(G, b, budget, err);
+        a = gfind(F, a, budget, err);
+        b = gfind(F, b, budget, err);
         if (a == b) return;
         if (budget < 0) { atomicOr(err, kErrGlobUnion); return; }
-        if (a > b) { int t = a; a = b; b = t; }
-        const int eb = (int)((uint32_t)b | kEncBit), ea = (int)((uint32_t)a | kEncBit);
-        if (atomicCAS(G + b, eb, ea) == eb) return;
+        if (gprio(a) < gprio(b)) { const gnode t = a; a = b; b = t; }
+        // link root b (lower priority) under root a; fails if b was linked meanwhile
+        if (atomicCAS(F.par(b), b, a) == b) return;
     }
 }
 

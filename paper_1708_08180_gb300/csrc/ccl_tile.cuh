@@ -23,8 +23,7 @@ struct SmemMerge {
     int P[kNodeCap];               // parent of each segment node
     uint16_t K[kNodeCap];          // key (smallest tile-local pixel index); for a
                                    // root reaching a seam, later its border slot
-    uint32_t Q[kQueueCap];         // unions left after the forest pass: a | b << 16;
-                                   // thread t owns slots t, t + 256, ... (no atomics)
+    uint32_t Q[kQueueCap];         // unions left after the forest pass: a | b << 16
     uint32_t flag[kNodeCap / 32];  // roots whose component reaches a tile seam
     uint32_t top[kThreads];        // first row of the strip, per word
     uint32_t bot[kThreads];        // last row of the strip, per word
@@ -32,6 +31,7 @@ struct SmemMerge {
     int base[kThreads];            // rank of the first segment starting in the word
     int warp_sums[kThreads / 32];
     int nborder;
+    int nq;
 };
 
 // Shared memory of the link phase.
@@ -138,8 +138,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         }
     }
     for (int i = tid; i < kNodeCap / 32; i += kThreads) sm.flag[i] = 0u;
-    for (int i = tid; i < kQueueCap; i += kThreads) sm.Q[i] = kQueueEmpty;
-    if (tid == 0) sm.nborder = 0;
+    if (tid == 0) { sm.nborder = 0; sm.nq = 0; }
     __syncthreads();
 
     // ---- a-2: union-find over the segments of the tile ----
@@ -152,7 +151,6 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     // unions are shared out evenly over the block (CAS link of the larger-key
     // root under the smaller).  (4) Every node is pointed straight at its root.
     int budget = kSmemHopBudget;
-    int nq = 0;   // this thread's queued unions (slots tid + 256 * k)
     if (s > 0) {
         const int up = tid - NW;
         const uint32_t av = sm.bot[up];
@@ -169,10 +167,9 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
                 lb = rb;
                 const int old = atomicCAS(&sm.P[rb], rb, ra);
                 if (old != rb && old != ra) {
-                    if (nq < kQueueCap / kThreads)
-                        sm.Q[(nq++) * kThreads + tid] = (uint32_t)ra | ((uint32_t)old << 16);
-                    else
-                        sunion(sm.P, sm.K, ra, old, budget, err);   // slots full: now
+                    const int q = atomicAdd(&sm.nq, 1);
+                    if (q < kQueueCap) sm.Q[q] = (uint32_t)ra | ((uint32_t)old << 16);
+                    else sunion(sm.P, sm.K, ra, old, budget, err);   // queue full: now
                 }
             };
             const uint32_t o = av & bv;
@@ -217,10 +214,15 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         }
         if (!__syncthreads_or(changed)) break;
     }
-    // (3) the queued unions, spread evenly over the block
-    for (int i = tid; i < kQueueCap; i += kThreads) {
-        const uint32_t e = sm.Q[i];
-        if (e != kQueueEmpty) sunion(sm.P, sm.K, (int)(e & 0xFFFFu), (int)(e >> 16), budget, err);
+    // (3) the queued unions, spread evenly over the block; most pairs already
+    // share a tree root after the jumping and are skipped without a union
+    {
+        const int nq = min(sm.nq, kQueueCap);
+        for (int i = tid; i < nq; i += kThreads) {
+            const uint32_t e = sm.Q[i];
+            const int pa = vP[e & 0xFFFFu], pb = vP[e >> 16];
+            if (pa != pb) sunion(sm.P, sm.K, pa, pb, budget, err);
+        }
     }
     __syncthreads();
 
@@ -239,67 +241,59 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     const bool has_up = ty > 0, has_down = ty < g.tiles_y - 1;
     const bool has_left = tx > 0, has_right = tx < g.tiles_x - 1;
 
-    // ---- seam records (top/bottom per column, left/right per strip) and flags ----
+    // ---- roots that reach a seam with a neighbouring tile ----
+    // Each record position (top/bottom row per column, left/right column per
+    // strip) remembers its segment's root; roots of positions that can touch
+    // a neighbour are flagged.
     auto mark = [&](int r) { atomicOr(&sm.flag[r >> 5], 1u << (r & 31)); };
+    int r_top = -1, r_bot = -1, r_left = -1, r_right = -1;
     if (tid < TW) {
         const int wc = tid >> 5, b = tid & 31;
         {   // top: strip 0
             const int o = wc;
-            const bool on = (sm.top[o] | sm.bot[o]) >> b & 1u;
-            int v = -1;
-            if (on) {
-                const int r = sm.P[seg_rank(sm.base[o], sm.st[o], b)];
-                v = gkey(sm.K[r]);
-                if (has_up && !local_only && ((sm.top[o] >> b) & 1u)) mark(r);
+            if ((sm.top[o] | sm.bot[o]) >> b & 1u) {
+                r_top = sm.P[seg_rank(sm.base[o], sm.st[o], b)];
+                if (has_up && !local_only && ((sm.top[o] >> b) & 1u)) mark(r_top);
             }
-            rec[tid] = v;
         }
         {   // bottom: strip NS-1
             const int o = (NS - 1) * NW + wc;
-            const bool on = (sm.top[o] | sm.bot[o]) >> b & 1u;
-            int v = -1;
-            if (on) {
-                const int r = sm.P[seg_rank(sm.base[o], sm.st[o], b)];
-                v = gkey(sm.K[r]);
-                if (has_down && !local_only && ((sm.bot[o] >> b) & 1u)) mark(r);
+            if ((sm.top[o] | sm.bot[o]) >> b & 1u) {
+                r_bot = sm.P[seg_rank(sm.base[o], sm.st[o], b)];
+                if (has_down && !local_only && ((sm.bot[o] >> b) & 1u)) mark(r_bot);
             }
-            rec[TW + tid] = v;
         }
     }
     if (tid < NS) {
         {   // left: column 0 of strip tid (always a segment start when set)
             const int o = tid * NW;
-            int v = -1;
             if ((sm.top[o] | sm.bot[o]) & 1u) {
-                const int r = sm.P[sm.base[o]];
-                v = gkey(sm.K[r]);
-                if (has_left && !local_only) mark(r);
+                r_left = sm.P[sm.base[o]];
+                if (has_left && !local_only) mark(r_left);
             }
-            rec[2 * TW + tid] = v;
         }
         {   // right: column TW-1 of strip tid
             const int o = tid * NW + NW - 1;
-            int v = -1;
             if ((sm.top[o] | sm.bot[o]) >> 31) {
-                const int r = sm.P[seg_rank(sm.base[o], sm.st[o], 31)];
-                v = gkey(sm.K[r]);
-                if (has_right && !local_only) mark(r);
+                r_right = sm.P[seg_rank(sm.base[o], sm.st[o], 31)];
+                if (has_right && !local_only) mark(r_right);
             }
-            rec[2 * TW + NS + tid] = v;
         }
     }
     __syncthreads();
     auto flagged = [&](int r) { return (sm.flag[r >> 5] >> (r & 31)) & 1u; };
 
-    // ---- border roots: list slot + global union-find root entry ----
+    // ---- border roots: a slot each, and a root node of the global forest ----
     if (!local_only) {
+        gnode *par = reinterpret_cast<gnode *>(tw_ + g.off_par);
         for (int n = tid; n < total; n += kThreads) {
             if (sm.P[n] == n && flagged(n)) {
                 const int j = atomicAdd(&sm.nborder, 1);
                 if (j < g.border_cap) {
                     const int gk = gkey(sm.K[n]);
-                    tw_[g.off_border + j] = gk;
-                    a.labels[gk] = (int)((uint32_t)gk | kEncBit);
+                    tw_[g.off_key + j] = gk;
+                    tw_[g.off_min + j] = gk;
+                    par[j] = make_gnode(tile, j);
                     sm.K[n] = (uint16_t)j;
                 } else {
                     atomicOr(err, kErrBorderCap);
@@ -307,6 +301,17 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             }
         }
         __syncthreads();
+    }
+
+    // ---- seam records: the border slot of each position's root ----
+    auto slot_of = [&](int r) { return (r >= 0 && flagged(r)) ? (int)sm.K[r] : -1; };
+    if (tid < TW) {
+        rec[tid] = slot_of(r_top);
+        rec[TW + tid] = slot_of(r_bot);
+    }
+    if (tid < NS) {
+        rec[2 * TW + tid] = slot_of(r_left);
+        rec[2 * TW + NS + tid] = slot_of(r_right);
     }
 
     // ---- per-segment labels ----
@@ -348,7 +353,7 @@ __host__ __device__ inline long long seam_items(const Geom &g) {
 constexpr int kSeamList = 128;   // pairs per warp before falling back to direct unions
 
 struct SmemSeams {
-    int2 list[kThreads / 32][kSeamList];
+    gnode list[kThreads / 32][kSeamList][2];
 };
 
 // Per-lane pair generator for item `idx` (horizontal: one 32-pixel word of a
@@ -358,32 +363,38 @@ struct SeamPairs {
     // horizontal state
     uint32_t os = 0, dr = 0, dl = 0;
     int xw = 0;
-    const int *up = nullptr, *dn = nullptr;
+    const int *up = nullptr, *dn = nullptr;   // record rows of tile (row, column 0)
+    long long tup = 0, tdn = 0;               // index of those tiles
     int tile_ints = 0, log2tw = 0, twm = 0;
     // vertical state: up to three candidate pairs
     int nv = 0, vi = 0;
-    int va0 = -1, vb0 = -1, va1 = -1, vb1 = -1, va2 = -1, vb2 = -1;
-    int la = -1, lb = -1;
+    gnode va0 = 0, vb0 = 0, va1 = 0, vb1 = 0, va2 = 0, vb2 = 0;
+    gnode la = ~0ull, lb = ~0ull;
+    bool bad = false;   // a seam record without a slot was met
 
-    __device__ __forceinline__ void push(int ka, int kb) {
+    __device__ __forceinline__ void push(gnode ka, gnode kb) {
         if (nv == 0) { va0 = ka; vb0 = kb; } else if (nv == 1) { va1 = ka; vb1 = kb; } else { va2 = ka; vb2 = kb; }
         ++nv;
     }
 
-    __device__ __forceinline__ int rec(const int *b, int xg) const {
-        return __ldcg(b + (size_t)(xg >> log2tw) * tile_ints + (xg & twm));
+    // node of the record at global column xg in the tile row starting at tile t0
+    // (kNoNode if the record holds no slot, which valid data never does)
+    __device__ __forceinline__ gnode rec(const int *b, long long t0, int xg) const {
+        const int c = xg >> log2tw;
+        const int slot = __ldcg(b + (size_t)c * tile_ints + (xg & twm));
+        return slot >= 0 ? make_gnode(t0 + c, slot) : kNoNode;
     }
-    __device__ __forceinline__ bool next(int &ka, int &kb) {
+    __device__ __forceinline__ bool next(gnode &ka, gnode &kb) {
         for (;;) {
             if (os) {
                 const int x = __ffs(os) - 1; os &= os - 1;
-                ka = rec(up, xw + x); kb = rec(dn, xw + x);
+                ka = rec(up, tup, xw + x); kb = rec(dn, tdn, xw + x);
             } else if (dr) {
                 const int x = __ffs(dr) - 1; dr &= dr - 1;
-                ka = rec(up, xw + x - 1); kb = rec(dn, xw + x);
+                ka = rec(up, tup, xw + x - 1); kb = rec(dn, tdn, xw + x);
             } else if (dl) {
                 const int x = __ffs(dl) - 1; dl &= dl - 1;
-                ka = rec(up, xw + x + 1); kb = rec(dn, xw + x);
+                ka = rec(up, tup, xw + x + 1); kb = rec(dn, tdn, xw + x);
             } else if (vi < nv) {
                 ka = vi == 0 ? va0 : vi == 1 ? va1 : va2;
                 kb = vi == 0 ? vb0 : vi == 1 ? vb1 : vb2;
@@ -391,6 +402,7 @@ struct SeamPairs {
             } else {
                 return false;
             }
+            if (ka == kNoNode || kb == kNoNode) { bad = true; continue; }
             if (ka != la || kb != lb) { la = ka; lb = kb; return true; }
         }
     }
@@ -414,8 +426,10 @@ __device__ __forceinline__ void seam_pairs_init(const ImageArgs &a, long long id
         const uint32_t bL = j > 0 ? (__ldcg(rb_ + j - 1) >> 31) : 0u;
         const uint32_t aR = j < g.nwg - 1 ? (__ldcg(ra_ + j + 1) & 1u) : 0u;
         const uint32_t bR = j < g.nwg - 1 ? (__ldcg(rb_ + j + 1) & 1u) : 0u;
-        sp.up = a.tws + (size_t)(ty - 1) * g.tiles_x * g.tile_ints + g.off_rec + g.tw;
-        sp.dn = a.tws + (size_t)ty * g.tiles_x * g.tile_ints + g.off_rec;
+        sp.tup = (long long)(ty - 1) * g.tiles_x;
+        sp.tdn = (long long)ty * g.tiles_x;
+        sp.up = a.tws + (size_t)sp.tup * g.tile_ints + g.off_rec + g.tw;
+        sp.dn = a.tws + (size_t)sp.tdn * g.tile_ints + g.off_rec;
         sp.tile_ints = g.tile_ints;
         sp.log2tw = g.log2tw;
         sp.twm = g.tw - 1;
@@ -437,8 +451,11 @@ __device__ __forceinline__ void seam_pairs_init(const ImageArgs &a, long long id
     const int x = tx * g.tw;
     const int r0 = ty * g.th + s * g.hs;
     if (r0 >= g.H) return;
-    const int *recL = a.tws + ((size_t)ty * g.tiles_x + (tx - 1)) * g.tile_ints + g.off_rec + 2 * g.tw + g.ns;
-    const int *recR = a.tws + ((size_t)ty * g.tiles_x + tx) * g.tile_ints + g.off_rec + 2 * g.tw;
+    const long long tL = (long long)ty * g.tiles_x + (tx - 1), tR = tL + 1;
+    const int *recL = a.tws + (size_t)tL * g.tile_ints + g.off_rec + 2 * g.tw + g.ns;
+    const int *recR = a.tws + (size_t)tR * g.tile_ints + g.off_rec + 2 * g.tw;
+    auto nL = [&](int ss) { const int v = __ldcg(recL + ss); return v >= 0 ? make_gnode(tL, v) : kNoNode; };
+    auto nR = [&](int ss) { const int v = __ldcg(recR + ss); return v >= 0 ? make_gnode(tR, v) : kNoNode; };
     const uint32_t l0 = bit_at(a.bits, g.nwg, r0, x - 1);
     const uint32_t rr0 = bit_at(a.bits, g.nwg, r0, x);
     uint32_t l1 = 0, rr1 = 0;
@@ -446,13 +463,13 @@ __device__ __forceinline__ void seam_pairs_init(const ImageArgs &a, long long id
         l1 = bit_at(a.bits, g.nwg, r0 + 1, x - 1);
         rr1 = bit_at(a.bits, g.nwg, r0 + 1, x);
     }
-    if ((l0 | l1) && (rr0 | rr1)) sp.push(__ldcg(recL + s), __ldcg(recR + s));
+    if ((l0 | l1) && (rr0 | rr1)) sp.push(nL(s), nR(s));
     if (g.hs == 2 && s > 0) {
         // diagonals between the last row of strip s-1 and the first of strip s
         const uint32_t lu = bit_at(a.bits, g.nwg, r0 - 1, x - 1);
         const uint32_t ru = bit_at(a.bits, g.nwg, r0 - 1, x);
-        if (lu && rr0) sp.push(__ldcg(recL + s - 1), __ldcg(recR + s));
-        if (l0 && ru) sp.push(__ldcg(recL + s), __ldcg(recR + s - 1));
+        if (lu && rr0) sp.push(nL(s - 1), nR(s));
+        if (l0 && ru) sp.push(nL(s), nR(s - 1));
     }
 }
 
@@ -460,44 +477,60 @@ __device__ __forceinline__ void seam_pairs_init(const ImageArgs &a, long long id
 __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, long long nitems,
                                            SmemSeams &sm, int *err) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const GlobalForest F{a.tws, a.g.tile_ints, a.g.off_par};
     int budget = kGlobHopBudget;
     SeamPairs sp;
     seam_pairs_init(a, idx0 + threadIdx.x, nitems, sp);
-    int2 *list = sm.list[warp];
+    gnode(*list)[2] = sm.list[warp];
     int n = 0;   // warp-uniform list length
     for (;;) {
-        int ka = -1, kb = -1;
+        gnode ka = 0, kb = 0;
         const bool have = sp.next(ka, kb);
         if (!__any_sync(0xFFFFFFFFu, have)) break;
-        const unsigned long long key =
-            have ? (((unsigned long long)(uint32_t)ka << 32) | (uint32_t)kb) : ~0ull;
+        // pairs are identified by (a, b) folded into 64 bits; equal keys are
+        // equal pairs or (rarely) a collision, which only skips a duplicate of
+        // a pair some lane still unions below
+        const unsigned long long key = have ? (ka * 0x9E3779B97F4A7C15ull) ^ kb : ~0ull;
         const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
-        const bool leader = have && (__ffs(same) - 1) == lane;
+        // the lowest lane of each key group leads; a lane whose pair differs
+        // from its leader's (a collision of the folded key) unions on its own
+        const int first = __ffs(same) - 1;
+        const bool leader = have && first == lane;
+        const gnode fa = __shfl_sync(0xFFFFFFFFu, ka, first);
+        const gnode fb = __shfl_sync(0xFFFFFFFFu, kb, first);
         const unsigned lead = __ballot_sync(0xFFFFFFFFu, leader);
+        if (have && !leader && (fa != ka || fb != kb)) gunion(F, ka, kb, budget, err);
         if (leader) {
             const int slot = n + __popc(lead & ((1u << lane) - 1u));
-            if (slot < kSeamList) list[slot] = make_int2(ka, kb);
-            else gunion(a.labels, ka, kb, budget, err);   // list full: union now
+            if (slot < kSeamList) { list[slot][0] = ka; list[slot][1] = kb; }
+            else gunion(F, ka, kb, budget, err);   // list full: union now
         }
         n += __popc(lead);
     }
+    if (sp.bad) atomicOr(err, kErrBorderCap);
     __syncwarp();
     const int m = n < kSeamList ? n : kSeamList;
-    for (int i = lane; i < m; i += 32) gunion(a.labels, list[i].x, list[i].y, budget, err);
+    for (int i = lane; i < m; i += 32) gunion(F, list[i][0], list[i][1], budget, err);
 }
 
 // ---------------------------------------------------------------------------
-// Resolve body (end of §II-B): the final label (1 + global root) of every
-// border root of tile `tile`, written over its slot in the border list, with
-// full path compression of the global array.  Run by one warp per tile after
-// all seam unions.
-__device__ __forceinline__ void resolve_tile(const ImageArgs &a, int tile, int lane, int *err) {
+// Resolve body (end of §II-B): after all seam unions, every border root of
+// tile `tile` finds its global root (compressing the path) and lowers the
+// root's set minimum to its own smallest raster index.  The link phase, a
+// kernel later, reads the minimum through the (now direct) parent link.
+// Run by one warp per tile.
+__device__ __forceinline__ void resolve_tile(const ImageArgs &a, long long tile, int lane,
+                                             int *err) {
+    const GlobalForest F{a.tws, a.g.tile_ints, a.g.off_par};
     int *tw_ = a.tws + (size_t)tile * a.g.tile_ints;
     const int nb = min(__ldcg(tw_), a.g.border_cap);
     int budget = kGlobHopBudget;
     for (int j = lane; j < nb; j += 32) {
-        const int key = __ldcg(tw_ + a.g.off_border + j);
-        tw_[a.g.off_border + j] = 1 + gfind(a.labels, key, budget, err);
+        const gnode r = gfind(F, make_gnode(tile, j), budget, err);
+        const int key = __ldcg(tw_ + a.g.off_key + j);
+        int *rmin = a.tws + (size_t)(r >> kSlotBits) * a.g.tile_ints + a.g.off_min +
+                    (int)(r & ((1u << kSlotBits) - 1u));
+        atomicMin(rmin, key);
     }
 }
 
@@ -531,7 +564,14 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
     const uint32_t st = m & ~((m << 1) | mL);
     const int *tw_ = a.tws + (size_t)tile * g.tile_ints;
     const int nb = min(__ldcg(tw_), g.border_cap);
-    for (int j = tid; j < nb; j += kThreads) sm.R[j] = __ldcg(tw_ + g.off_border + j);
+    {
+        const gnode *par = reinterpret_cast<const gnode *>(tw_ + g.off_par);
+        for (int j = tid; j < nb; j += kThreads) {
+            const gnode r = __ldcg(par + j);   // the global root after the resolve pass
+            sm.R[j] = 1 + __ldcg(a.tws + (size_t)(r >> kSlotBits) * g.tile_ints + g.off_min +
+                                 (int)(r & ((1u << kSlotBits) - 1u)));
+        }
+    }
     int total;
     const int base = block_excl_scan(__popc(st), sm.warp_sums, total);   // syncs: R visible
     sm.st[tid] = st;
