@@ -61,10 +61,9 @@ constexpr int kGlobHopBudget = 1 << 20;   // per thread per work item (global me
 // workspace (all offsets in ints from the tile's base):
 //   [0, kHdrInts)               header: [0] = number of border roots
 //   [kHdrInts, off_key)         label of each segment node (node_cap)
-//   [off_key, off_min)          smallest raster index of each border root's component
+//   [off_key, off_fin)          smallest raster index of each border root's component
 //                               inside the tile (border_cap)
-//   [off_min, off_par)          smallest raster index of its global set, valid at a
-//                               global root once the resolve pass has run (border_cap)
+//   [off_fin, off_par)          final label of each border root (resolve pass)
 //   [off_par, off_rec)          parent of each border root in the global forest,
 //                               64-bit node ids (border_cap x 2 ints, 8-byte aligned)
 //   [off_rec, off_rec + rec)    seam records, border slot of the root (-1: none):
@@ -80,7 +79,7 @@ struct Geom {
     int nwg;        // words per bit-image row = ceil(W / 32)
     int node_cap;   // most segment nodes a tile of this image can hold
     int border_cap; // most border roots
-    int off_key, off_min, off_par, off_rec, tile_ints;
+    int off_key, off_fin, off_par, off_rec, tile_ints;
 };
 
 __host__ __device__ inline Geom make_geom(int H, int W, int conn, int tile_w) {
@@ -102,8 +101,8 @@ __host__ __device__ inline Geom make_geom(int H, int W, int conn, int tile_w) {
     g.node_cap = g.ns * per_strip;
     g.border_cap = 2 * per_strip + 2 * g.ns;
     g.off_key = kHdrInts + g.node_cap;
-    g.off_min = g.off_key + g.border_cap;
-    g.off_par = (g.off_min + g.border_cap + 1) & ~1;
+    g.off_fin = g.off_key + g.border_cap;
+    g.off_par = (g.off_fin + g.border_cap + 1) & ~1;
     g.off_rec = g.off_par + 2 * g.border_cap;
     g.tile_ints = (g.off_rec + 2 * g.tw + 2 * g.ns + 63) & ~63;   // 256-byte multiple
     return g;
@@ -246,11 +245,13 @@ __device__ __forceinline__ void sunion(int *P, const uint16_t *K, int a, int b, 
 
 // ---------------------------------------------------------------------------
 // union-find in global memory over the border roots of all tiles.  A node is
-// (tile << kSlotBits | slot), 64-bit; its parent lives in the owning tile's
-// workspace.  Roots are linked by a fixed pseudo-random priority of the node
-// id (randomised linking keeps the forest shallow when thousands of tiles
-// merge at once, where "link to the smaller index" builds long chains); the
-// smallest raster index of each set is gathered separately (resolve pass).
+// (tile << kSlotBits | slot), 64-bit; its parent and its key (smallest raster
+// index of its component inside the tile) live in the owning tile's
+// workspace.  Links go from the root with the larger key to the root with the
+// smaller, so every root carries its set's smallest raster index (as the
+// paper's atomicMin linking does); and the root of a component spanning many
+// tiles settles at once on the image-wide minimum, so concurrent unions link
+// other roots under it instead of contending for it.
 
 typedef unsigned long long gnode;
 constexpr gnode kNoNode = ~0ull;
@@ -259,43 +260,40 @@ __device__ __forceinline__ gnode make_gnode(long long tile, int slot) {
     return ((gnode)tile << kSlotBits) | (gnode)slot;
 }
 
-// priority: a bijective 64-bit mix (SplitMix64 finaliser, Steele et al. 2014)
-__device__ __forceinline__ unsigned long long gprio(gnode x) {
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-    return x ^ (x >> 31);
-}
-
 struct GlobalForest {
     int *tws;
-    int tile_ints, off_par;
+    int tile_ints, off_par, off_key;
+    __device__ __forceinline__ int *base(gnode n) const {
+        return tws + (size_t)(n >> kSlotBits) * tile_ints;
+    }
     __device__ __forceinline__ gnode *par(gnode n) const {
-        return reinterpret_cast<gnode *>(tws + (size_t)(n >> kSlotBits) * tile_ints + off_par) +
-               (n & ((1u << kSlotBits) - 1u));
+        return reinterpret_cast<gnode *>(base(n) + off_par) + (n & ((1u << kSlotBits) - 1u));
+    }
+    __device__ __forceinline__ int key(gnode n) const {
+        return __ldcg(base(n) + off_key + (int)(n & ((1u << kSlotBits) - 1u)));
     }
 };
 
 __device__ __forceinline__ gnode gfind(const GlobalForest &F, gnode x, int &budget, int *err) {
-    // walk to the root r ...
-    gnode r = x;
+    // Walk to the root, remembering the first two nodes passed whose parent
+    // is not the root, then point those at the root.  Keys strictly decrease
+    // along parent links, so a node seen below the root always has a larger
+    // key than the root: the new link can never close a cycle, whatever other
+    // threads did to the path meanwhile.
+    gnode w0 = kNoNode, w1 = kNoNode;
+    gnode r = x, prev = kNoNode;
     for (;;) {
         if (--budget < 0) { atomicOr(err, kErrGlobFind); return r; }
         const gnode p = __ldcg(F.par(r));
         if (p == r) break;
+        if (prev != kNoNode) {   // prev -> r -> p: prev's parent is not the root
+            if (w0 == kNoNode) w0 = prev; else if (w1 == kNoNode) w1 = prev;
+        }
+        prev = r;
         r = p;
     }
-    // ... then point the walked nodes at r.  Priorities strictly increase
-    // along parent links, so only nodes below r (lower priority) are
-    // rewritten: a path another thread has meanwhile compressed past r is left
-    // alone instead of being pointed back down (which would close a cycle).
-    const unsigned long long pr = gprio(r);
-    while (x != r) {
-        if (--budget < 0) { atomicOr(err, kErrGlobFind); return r; }
-        const gnode p = __ldcg(F.par(x));
-        if (p == r || gprio(p) >= pr) break;
-        __stcg(F.par(x), r);   // x is not a root: no link can target it
-        x = p;
-    }
+    if (w0 != kNoNode) __stcg(F.par(w0), r);
+    if (w1 != kNoNode) __stcg(F.par(w1), r);
     return r;
 }
 
@@ -306,8 +304,8 @@ __device__ __forceinline__ void gunion(const GlobalForest &F, gnode a, gnode b, 
         b = gfind(F, b, budget, err);
         if (a == b) return;
         if (budget < 0) { atomicOr(err, kErrGlobUnion); return; }
-        if (gprio(a) < gprio(b)) { const gnode t = a; a = b; b = t; }
-        // link root b (lower priority) under root a; fails if b was linked meanwhile
+        if (F.key(a) > F.key(b)) { const gnode t = a; a = b; b = t; }
+        // link root b (larger key) under root a; fails if b was linked meanwhile
         if (atomicCAS(F.par(b), b, a) == b) return;
     }
 }

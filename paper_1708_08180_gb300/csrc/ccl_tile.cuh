@@ -292,7 +292,6 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
                 if (j < g.border_cap) {
                     const int gk = gkey(sm.K[n]);
                     tw_[g.off_key + j] = gk;
-                    tw_[g.off_min + j] = gk;
                     par[j] = make_gnode(tile, j);
                     sm.K[n] = (uint16_t)j;
                 } else {
@@ -477,7 +476,7 @@ __device__ __forceinline__ void seam_pairs_init(const ImageArgs &a, long long id
 __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, long long nitems,
                                            SmemSeams &sm, int *err) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const GlobalForest F{a.tws, a.g.tile_ints, a.g.off_par};
+    const GlobalForest F{a.tws, a.g.tile_ints, a.g.off_par, a.g.off_key};
     int budget = kGlobHopBudget;
     SeamPairs sp;
     seam_pairs_init(a, idx0 + threadIdx.x, nitems, sp);
@@ -515,22 +514,17 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
 
 // ---------------------------------------------------------------------------
 // Resolve body (end of §II-B): after all seam unions, every border root of
-// tile `tile` finds its global root (compressing the path) and lowers the
-// root's set minimum to its own smallest raster index.  The link phase, a
-// kernel later, reads the minimum through the (now direct) parent link.
-// Run by one warp per tile.
+// tile `tile` finds its global root (compressing the path) and stores its
+// final label, 1 + the root's key.  Run by one warp per tile.
 __device__ __forceinline__ void resolve_tile(const ImageArgs &a, long long tile, int lane,
                                              int *err) {
-    const GlobalForest F{a.tws, a.g.tile_ints, a.g.off_par};
+    const GlobalForest F{a.tws, a.g.tile_ints, a.g.off_par, a.g.off_key};
     int *tw_ = a.tws + (size_t)tile * a.g.tile_ints;
     const int nb = min(__ldcg(tw_), a.g.border_cap);
     int budget = kGlobHopBudget;
     for (int j = lane; j < nb; j += 32) {
         const gnode r = gfind(F, make_gnode(tile, j), budget, err);
-        const int key = __ldcg(tw_ + a.g.off_key + j);
-        int *rmin = a.tws + (size_t)(r >> kSlotBits) * a.g.tile_ints + a.g.off_min +
-                    (int)(r & ((1u << kSlotBits) - 1u));
-        atomicMin(rmin, key);
+        tw_[a.g.off_fin + j] = 1 + F.key(r);
     }
 }
 
@@ -564,14 +558,7 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
     const uint32_t st = m & ~((m << 1) | mL);
     const int *tw_ = a.tws + (size_t)tile * g.tile_ints;
     const int nb = min(__ldcg(tw_), g.border_cap);
-    {
-        const gnode *par = reinterpret_cast<const gnode *>(tw_ + g.off_par);
-        for (int j = tid; j < nb; j += kThreads) {
-            const gnode r = __ldcg(par + j);   // the global root after the resolve pass
-            sm.R[j] = 1 + __ldcg(a.tws + (size_t)(r >> kSlotBits) * g.tile_ints + g.off_min +
-                                 (int)(r & ((1u << kSlotBits) - 1u)));
-        }
-    }
+    for (int j = tid; j < nb; j += kThreads) sm.R[j] = __ldcg(tw_ + g.off_fin + j);
     int total;
     const int base = block_excl_scan(__popc(st), sm.warp_sums, total);   // syncs: R visible
     sm.st[tid] = st;
