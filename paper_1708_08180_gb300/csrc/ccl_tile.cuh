@@ -323,9 +323,10 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
 }
 
 // ---------------------------------------------------------------------------
-// Kernel 2 body: seam unions (§II-B).  Work items: the horizontal seams'
-// words (rows y-1, y with y = ty*TH), (tiles_y-1)*nwg of them, padded to a
-// multiple of 256 so that no warp or 256-item chunk mixes the two kinds; then
+// Kernel 2 body: seam unions (§II-B).  Work items: 8-column groups of the
+// horizontal seams (rows y-1, y with y = ty*TH), (tiles_y-1)*nwg*4 of them,
+// padded to a multiple of 256 so that no warp or 256-item chunk mixes the two
+// kinds; then
 // one item per strip of each vertical seam, (tiles_x-1)*tiles_y*NS.  Each
 // touching pair of runs across a seam yields one union of the two local roots
 // (deduplicated per block of 256 items, see seam_block).
@@ -333,8 +334,16 @@ __device__ __forceinline__ uint32_t bit_at(const uint32_t *bits, int nwg, int y,
     return (__ldcg(bits + (size_t)y * nwg + (x >> 5)) >> (x & 31)) & 1u;
 }
 
+// horizontal seam items cover 8 columns each (4 per 32-bit word): about two
+// contacts per thread at p = 0.5, so a warp waits on few dependent loads
+constexpr int kSeamGroupsPerWord = 4;
+
+__host__ __device__ inline long long seam_h_real(const Geom &g) {
+    return (long long)(g.tiles_y - 1) * g.nwg * kSeamGroupsPerWord;
+}
+
 __host__ __device__ inline long long seam_h_items(const Geom &g) {
-    return ((long long)(g.tiles_y - 1) * g.nwg + 255) / 256 * 256;
+    return (seam_h_real(g) + 255) / 256 * 256;
 }
 
 __host__ __device__ inline long long seam_items(const Geom &g) {
@@ -410,17 +419,20 @@ struct SeamPairs {
 __device__ __forceinline__ void seam_pairs_init(const ImageArgs &a, long long idx,
                                                 long long nitems, SeamPairs &sp) {
     const Geom &g = a.g;
-    const long long nh_real = (long long)(g.tiles_y - 1) * g.nwg;
+    const long long nh_real = seam_h_real(g);
     const long long nh = seam_h_items(g);
     if (idx < nh) {
         if (idx >= nh_real) return;
-        const int ty = (int)(idx / g.nwg) + 1;
-        const int j = (int)(idx % g.nwg);
+        const long long per_row = (long long)g.nwg * kSeamGroupsPerWord;
+        const int ty = (int)(idx / per_row) + 1;
+        const int grp = (int)(idx % per_row);
+        const int j = grp / kSeamGroupsPerWord;
+        const uint32_t gmask = 0xFFu << (8 * (grp % kSeamGroupsPerWord));
         const int y = ty * g.th;
         const uint32_t *ra_ = a.bits + (size_t)(y - 1) * g.nwg;
         const uint32_t *rb_ = a.bits + (size_t)y * g.nwg;
         const uint32_t av = __ldcg(ra_ + j), bv = __ldcg(rb_ + j);
-        if (!bv) return;   // every contact needs a pixel in row y
+        if (!(bv & gmask)) return;   // every contact needs a pixel of row y in the group
         const uint32_t aL = j > 0 ? (__ldcg(ra_ + j - 1) >> 31) : 0u;
         const uint32_t bL = j > 0 ? (__ldcg(rb_ + j - 1) >> 31) : 0u;
         const uint32_t aR = j < g.nwg - 1 ? (__ldcg(ra_ + j + 1) & 1u) : 0u;
@@ -434,10 +446,10 @@ __device__ __forceinline__ void seam_pairs_init(const ImageArgs &a, long long id
         sp.twm = g.tw - 1;
         sp.xw = 32 * j;
         const uint32_t o = av & bv;
-        sp.os = o & ~((o << 1) | (aL & bL));
+        sp.os = o & ~((o << 1) | (aL & bL)) & gmask;
         if (g.hs == 2) {
-            sp.dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
-            sp.dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31));
+            sp.dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL) & gmask;
+            sp.dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31)) & gmask;
         }
         return;
     }
