@@ -191,6 +191,7 @@ bool plan(const ccl_image *imgs, int n, int conn, Layout &L) {
         if (!im.d_img || !im.d_labels || !valid_image_dims(im.height, im.width)) return false;
         const Geom g = make_geom(im.height, im.width, conn,
                                  default_tile_width(im.height, im.width, conn));
+        if (!geom_fits(g)) return false;
         L.geom[k] = g;
         L.img_off[k] = off;
         // sized for the widest need over all tile widths: a workspace sized

@@ -39,7 +39,9 @@ constexpr int kBorderCapMax = 576;        // border segments: <= 2*16*NW + 2*NS 
 constexpr int kHdrInts = 4;               // [0] = border-root count
 
 constexpr int kQueueCap = 2048;           // unions left after the local forest pass
-constexpr int kSlotBits = 10;             // global node = tile << kSlotBits | border slot
+constexpr int kSlotBits = 10;             // border slots per tile < 2^10
+constexpr int kTileBits = 23;             // tiles per image < 2^23
+constexpr long long kMaxTiles = 1ll << kTileBits;
 
 // device error word bits
 constexpr int kErrSmemFind = 1;
@@ -66,8 +68,9 @@ constexpr int kGlobHopBudget = 1 << 20;   // per thread per work item (global me
 //   [off_fin, off_par)          final label of each border root (resolve pass)
 //   [off_par, off_rec)          parent of each border root in the global forest,
 //                               64-bit node ids (border_cap x 2 ints, 8-byte aligned)
-//   [off_rec, off_rec + rec)    seam records, border slot of the root (-1: none):
-//                               top[tw], bottom[tw], left[ns], right[ns]
+//   [off_rec, off_rec + rec)    seam records, global node of the position's root
+//                               (64-bit; all ones: none): top[tw], bottom[tw],
+//                               left[ns], right[ns]
 struct Geom {
     int H, W;
     int nw;         // 32-bit words per tile row: 1, 2, 4, 8
@@ -92,9 +95,9 @@ __host__ __device__ inline Geom make_geom(int H, int W, int conn, int tile_w) {
     g.tw = tile_w;
     g.th = g.ns * g.hs;
     g.log2tw = tile_w == 32 ? 5 : tile_w == 64 ? 6 : tile_w == 128 ? 7 : 8;
-    g.tiles_x = (W + g.tw - 1) / g.tw;
-    g.tiles_y = (H + g.th - 1) / g.th;
-    g.nwg = (W + 31) / 32;
+    g.tiles_x = (int)(((long long)W + g.tw - 1) / g.tw);
+    g.tiles_y = (int)(((long long)H + g.th - 1) / g.th);
+    g.nwg = (int)(((long long)W + 31) / 32);
     // a strip row of c valid columns holds at most ceil(c / 2) runs
     const int cols = W < g.tw ? W : g.tw;
     const int per_strip = (cols + 1) / 2;
@@ -104,8 +107,13 @@ __host__ __device__ inline Geom make_geom(int H, int W, int conn, int tile_w) {
     g.off_fin = g.off_key + g.border_cap;
     g.off_par = (g.off_fin + g.border_cap + 1) & ~1;
     g.off_rec = g.off_par + 2 * g.border_cap;
-    g.tile_ints = (g.off_rec + 2 * g.tw + 2 * g.ns + 63) & ~63;   // 256-byte multiple
+    g.tile_ints = (g.off_rec + 2 * (2 * g.tw + 2 * g.ns) + 63) & ~63;   // 256-byte multiple
     return g;
+}
+
+// the (tile, slot) fields of a global node id hold every tile of the image
+__host__ __device__ inline bool geom_fits(const Geom &g) {
+    return (long long)g.tiles_x * g.tiles_y <= kMaxTiles;
 }
 
 __host__ __device__ inline size_t bits_bytes(const Geom &g) {
@@ -244,33 +252,33 @@ __device__ __forceinline__ void sunion(int *P, const uint16_t *K, int a, int b, 
 }
 
 // ---------------------------------------------------------------------------
-// union-find in global memory over the border roots of all tiles.  A node is
-// (tile << kSlotBits | slot), 64-bit; its parent and its key (smallest raster
-// index of its component inside the tile) live in the owning tile's
-// workspace.  Links go from the root with the larger key to the root with the
-// smaller, so every root carries its set's smallest raster index (as the
-// paper's atomicMin linking does); and the root of a component spanning many
-// tiles settles at once on the image-wide minimum, so concurrent unions link
-// other roots under it instead of contending for it.
+// union-find in global memory over the border roots of all tiles.  A node id
+// is 64-bit: key << 33 | tile << 10 | slot, where key is the smallest raster
+// index of the root's component inside its tile; its parent lives in the
+// owning tile's workspace.  Comparing ids compares keys (keys are distinct),
+// so linking the larger id under the smaller keeps every root at its set's
+// smallest raster index (as the paper's atomicMin linking does) with no key
+// loads; and the root of a component spanning many tiles settles at once on
+// the image-wide minimum, so concurrent unions link other roots under it
+// instead of contending for it.
 
 typedef unsigned long long gnode;
 constexpr gnode kNoNode = ~0ull;
 
-__device__ __forceinline__ gnode make_gnode(long long tile, int slot) {
-    return ((gnode)tile << kSlotBits) | (gnode)slot;
+__device__ __forceinline__ gnode make_gnode(int key, long long tile, int slot) {
+    return ((gnode)(uint32_t)key << (kTileBits + kSlotBits)) | ((gnode)tile << kSlotBits) |
+           (gnode)slot;
 }
+
+__device__ __forceinline__ int gnode_key(gnode n) { return (int)(n >> (kTileBits + kSlotBits)); }
 
 struct GlobalForest {
     int *tws;
-    int tile_ints, off_par, off_key;
-    __device__ __forceinline__ int *base(gnode n) const {
-        return tws + (size_t)(n >> kSlotBits) * tile_ints;
-    }
+    int tile_ints, off_par;
     __device__ __forceinline__ gnode *par(gnode n) const {
-        return reinterpret_cast<gnode *>(base(n) + off_par) + (n & ((1u << kSlotBits) - 1u));
-    }
-    __device__ __forceinline__ int key(gnode n) const {
-        return __ldcg(base(n) + off_key + (int)(n & ((1u << kSlotBits) - 1u)));
+        const long long tile = (long long)((n >> kSlotBits) & (kMaxTiles - 1));
+        return reinterpret_cast<gnode *>(tws + (size_t)tile * tile_ints + off_par) +
+               (n & ((1u << kSlotBits) - 1u));
     }
 };
 
@@ -304,7 +312,7 @@ __device__ __forceinline__ void gunion(const GlobalForest &F, gnode a, gnode b, 
         b = gfind(F, b, budget, err);
         if (a == b) return;
         if (budget < 0) { atomicOr(err, kErrGlobUnion); return; }
-        if (F.key(a) > F.key(b)) { const gnode t = a; a = b; b = t; }
+        if (a > b) { const gnode t = a; a = b; b = t; }
         // link root b (larger key) under root a; fails if b was linked meanwhile
         if (atomicCAS(F.par(b), b, a) == b) return;
     }

@@ -107,6 +107,7 @@ ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, in
     if (!valid_tile_w(tile_w)) return CCL_ERR_INVALID_ARG;
     if (flags & ~(unsigned)CCL_FLAG_LOCAL_ONLY) return CCL_ERR_INVALID_ARG;
     const Geom g = make_geom(height, width, conn, tile_w);
+    if (!geom_fits(g)) return CCL_ERR_INVALID_ARG;
     // the documented contract: ccl_workspace_bytes() for the default tile
     // width (it does not depend on the current table), the exact need otherwise
     const size_t need = default_tile ? ccl_workspace_bytes(height, width, conn)
@@ -162,6 +163,7 @@ extern "C" size_t ccl_workspace_bytes_tiled(int height, int width, int connectiv
     if (tile_w == 0) return ccl_workspace_bytes(height, width, connectivity);
     if (!ccl::valid_tile_w(tile_w)) return 0;
     const ccl::Geom g = ccl::make_geom(height, width, connectivity, tile_w);
+    if (!ccl::geom_fits(g)) return 0;
     return ccl::bits_bytes(g) + ccl::tiles_bytes(g);
 }
 

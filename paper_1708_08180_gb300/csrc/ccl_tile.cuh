@@ -292,7 +292,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
                 if (j < g.border_cap) {
                     const int gk = gkey(sm.K[n]);
                     tw_[g.off_key + j] = gk;
-                    par[j] = make_gnode(tile, j);
+                    par[j] = make_gnode(gk, tile, j);
                     sm.K[n] = (uint16_t)j;
                 } else {
                     atomicOr(err, kErrBorderCap);
@@ -302,15 +302,19 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         __syncthreads();
     }
 
-    // ---- seam records: the border slot of each position's root ----
-    auto slot_of = [&](int r) { return (r >= 0 && flagged(r)) ? (int)sm.K[r] : -1; };
+    // ---- seam records: the global node of each position's root ----
+    long long *rec64 = reinterpret_cast<long long *>(rec);
+    auto node_of = [&](int r) {
+        return (r >= 0 && flagged(r)) ? (long long)make_gnode(tw_[g.off_key + sm.K[r]], tile, sm.K[r])
+                                      : (long long)kNoNode;
+    };
     if (tid < TW) {
-        rec[tid] = slot_of(r_top);
-        rec[TW + tid] = slot_of(r_bot);
+        rec64[tid] = node_of(r_top);
+        rec64[TW + tid] = node_of(r_bot);
     }
     if (tid < NS) {
-        rec[2 * TW + tid] = slot_of(r_left);
-        rec[2 * TW + NS + tid] = slot_of(r_right);
+        rec64[2 * TW + tid] = node_of(r_left);
+        rec64[2 * TW + NS + tid] = node_of(r_right);
     }
 
     // ---- per-segment labels ----
@@ -371,8 +375,7 @@ struct SeamPairs {
     // horizontal state
     uint32_t os = 0, dr = 0, dl = 0;
     int xw = 0;
-    const int *up = nullptr, *dn = nullptr;   // record rows of tile (row, column 0)
-    long long tup = 0, tdn = 0;               // index of those tiles
+    const long long *up = nullptr, *dn = nullptr;   // record rows of tile (row, column 0)
     int tile_ints = 0, log2tw = 0, twm = 0;
     // vertical state: up to three candidate pairs
     int nv = 0, vi = 0;
@@ -386,23 +389,21 @@ struct SeamPairs {
     }
 
     // node of the record at global column xg in the tile row starting at tile t0
-    // (kNoNode if the record holds no slot, which valid data never does)
-    __device__ __forceinline__ gnode rec(const int *b, long long t0, int xg) const {
-        const int c = xg >> log2tw;
-        const int slot = __ldcg(b + (size_t)c * tile_ints + (xg & twm));
-        return slot >= 0 ? make_gnode(t0 + c, slot) : kNoNode;
+    // (kNoNode if the record holds no node, which valid data never does)
+    __device__ __forceinline__ gnode rec(const long long *b, int xg) const {
+        return (gnode)__ldcg(b + (size_t)(xg >> log2tw) * (tile_ints / 2) + (xg & twm));
     }
     __device__ __forceinline__ bool next(gnode &ka, gnode &kb) {
         for (;;) {
             if (os) {
                 const int x = __ffs(os) - 1; os &= os - 1;
-                ka = rec(up, tup, xw + x); kb = rec(dn, tdn, xw + x);
+                ka = rec(up, xw + x); kb = rec(dn, xw + x);
             } else if (dr) {
                 const int x = __ffs(dr) - 1; dr &= dr - 1;
-                ka = rec(up, tup, xw + x - 1); kb = rec(dn, tdn, xw + x);
+                ka = rec(up, xw + x - 1); kb = rec(dn, xw + x);
             } else if (dl) {
                 const int x = __ffs(dl) - 1; dl &= dl - 1;
-                ka = rec(up, tup, xw + x + 1); kb = rec(dn, tdn, xw + x);
+                ka = rec(up, xw + x + 1); kb = rec(dn, xw + x);
             } else if (vi < nv) {
                 ka = vi == 0 ? va0 : vi == 1 ? va1 : va2;
                 kb = vi == 0 ? vb0 : vi == 1 ? vb1 : vb2;
@@ -437,10 +438,10 @@ __device__ __forceinline__ void seam_pairs_init(const ImageArgs &a, long long id
         const uint32_t bL = j > 0 ? (__ldcg(rb_ + j - 1) >> 31) : 0u;
         const uint32_t aR = j < g.nwg - 1 ? (__ldcg(ra_ + j + 1) & 1u) : 0u;
         const uint32_t bR = j < g.nwg - 1 ? (__ldcg(rb_ + j + 1) & 1u) : 0u;
-        sp.tup = (long long)(ty - 1) * g.tiles_x;
-        sp.tdn = (long long)ty * g.tiles_x;
-        sp.up = a.tws + (size_t)sp.tup * g.tile_ints + g.off_rec + g.tw;
-        sp.dn = a.tws + (size_t)sp.tdn * g.tile_ints + g.off_rec;
+        sp.up = reinterpret_cast<const long long *>(
+                    a.tws + (size_t)(ty - 1) * g.tiles_x * g.tile_ints + g.off_rec) + g.tw;
+        sp.dn = reinterpret_cast<const long long *>(
+                    a.tws + (size_t)ty * g.tiles_x * g.tile_ints + g.off_rec);
         sp.tile_ints = g.tile_ints;
         sp.log2tw = g.log2tw;
         sp.twm = g.tw - 1;
@@ -463,10 +464,12 @@ __device__ __forceinline__ void seam_pairs_init(const ImageArgs &a, long long id
     const int r0 = ty * g.th + s * g.hs;
     if (r0 >= g.H) return;
     const long long tL = (long long)ty * g.tiles_x + (tx - 1), tR = tL + 1;
-    const int *recL = a.tws + (size_t)tL * g.tile_ints + g.off_rec + 2 * g.tw + g.ns;
-    const int *recR = a.tws + (size_t)tR * g.tile_ints + g.off_rec + 2 * g.tw;
-    auto nL = [&](int ss) { const int v = __ldcg(recL + ss); return v >= 0 ? make_gnode(tL, v) : kNoNode; };
-    auto nR = [&](int ss) { const int v = __ldcg(recR + ss); return v >= 0 ? make_gnode(tR, v) : kNoNode; };
+    const long long *recL =
+        reinterpret_cast<const long long *>(a.tws + (size_t)tL * g.tile_ints + g.off_rec) + 2 * g.tw + g.ns;
+    const long long *recR =
+        reinterpret_cast<const long long *>(a.tws + (size_t)tR * g.tile_ints + g.off_rec) + 2 * g.tw;
+    auto nL = [&](int ss) { return (gnode)__ldcg(recL + ss); };
+    auto nR = [&](int ss) { return (gnode)__ldcg(recR + ss); };
     const uint32_t l0 = bit_at(a.bits, g.nwg, r0, x - 1);
     const uint32_t rr0 = bit_at(a.bits, g.nwg, r0, x);
     uint32_t l1 = 0, rr1 = 0;
@@ -488,7 +491,7 @@ __device__ __forceinline__ void seam_pairs_init(const ImageArgs &a, long long id
 __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, long long nitems,
                                            SmemSeams &sm, int *err) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const GlobalForest F{a.tws, a.g.tile_ints, a.g.off_par, a.g.off_key};
+    const GlobalForest F{a.tws, a.g.tile_ints, a.g.off_par};
     int budget = kGlobHopBudget;
     SeamPairs sp;
     seam_pairs_init(a, idx0 + threadIdx.x, nitems, sp);
@@ -530,13 +533,14 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
 // final label, 1 + the root's key.  Run by one warp per tile.
 __device__ __forceinline__ void resolve_tile(const ImageArgs &a, long long tile, int lane,
                                              int *err) {
-    const GlobalForest F{a.tws, a.g.tile_ints, a.g.off_par, a.g.off_key};
+    const GlobalForest F{a.tws, a.g.tile_ints, a.g.off_par};
     int *tw_ = a.tws + (size_t)tile * a.g.tile_ints;
     const int nb = min(__ldcg(tw_), a.g.border_cap);
     int budget = kGlobHopBudget;
+    const gnode *par = reinterpret_cast<const gnode *>(tw_ + a.g.off_par);
     for (int j = lane; j < nb; j += 32) {
-        const gnode r = gfind(F, make_gnode(tile, j), budget, err);
-        tw_[a.g.off_fin + j] = 1 + F.key(r);
+        const gnode r = gfind(F, __ldcg(par + j), budget, err);
+        tw_[a.g.off_fin + j] = 1 + gnode_key(r);
     }
 }
 
