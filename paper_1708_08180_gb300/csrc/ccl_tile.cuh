@@ -205,31 +205,54 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     __syncthreads();
     // (2) pointer jumping until every node points at its tree's root
     volatile int *vP = sm.P;
+    auto jump = [&]() {
+        for (int round = 0; round < 64; ++round) {
+            int changed = 0;
+            for (int n = tid; n < total; n += kThreads) {
+                const int p = vP[n];
+                const int gp = vP[p];
+                if (gp != p) { vP[n] = gp; changed = 1; }
+            }
+            if (!__syncthreads_or(changed)) return;
+        }
+        atomicOr(err, kErrSmemFind);
+    };
+    jump();
+    // (3) hook and jump: each queued pair whose roots differ hooks the root
+    // with the larger key under the other (one CAS, no find); a hook that
+    // loses a race is queued again with the loser's new parent.  Pointer
+    // jumping then flattens the forest, and rounds repeat until no pair is
+    // left.  The final jumping leaves every node pointing at its root.
+    constexpr int kPer = kQueueCap / kThreads;   // queue entries per thread per round
     for (int round = 0; round < 64; ++round) {
-        int changed = 0;
-        for (int n = tid; n < total; n += kThreads) {
-            const int p = vP[n];
-            const int gp = vP[p];
-            if (gp != p) { vP[n] = gp; changed = 1; }
+        const int nq = min(sm.nq, kQueueCap);   // block-uniform: read after a barrier
+        if (nq == 0) break;
+        uint32_t e[kPer];
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int i = tid + k * kThreads;
+            e[k] = i < nq ? sm.Q[i] : 0xFFFFFFFFu;
         }
-        if (!__syncthreads_or(changed)) break;
-    }
-    // (3) the queued unions, spread evenly over the block; most pairs already
-    // share a tree root after the jumping and are skipped without a union
-    {
-        const int nq = min(sm.nq, kQueueCap);
-        for (int i = tid; i < nq; i += kThreads) {
-            const uint32_t e = sm.Q[i];
-            const int pa = vP[e & 0xFFFFu], pb = vP[e >> 16];
-            if (pa != pb) sunion(sm.P, sm.K, pa, pb, budget, err);
+        __syncthreads();
+        if (tid == 0) sm.nq = 0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            if (e[k] == 0xFFFFFFFFu) continue;
+            int pa = vP[e[k] & 0xFFFFu], pb = vP[e[k] >> 16];
+            if (pa == pb) continue;
+            if (sm.K[pa] > sm.K[pb]) { const int t = pa; pa = pb; pb = t; }
+            const int old = atomicCAS(&sm.P[pb], pb, pa);   // hook root pb under pa
+            if (old != pb && old != pa) {
+                const int q = atomicAdd(&sm.nq, 1);
+                if (q < kQueueCap) sm.Q[q] = (uint32_t)pa | ((uint32_t)old << 16);
+                else sunion(sm.P, sm.K, pa, old, budget, err);   // queue full: now
+            }
         }
+        __syncthreads();
+        jump();
     }
-    __syncthreads();
-
-    // ---- (4) roots: every node points straight at its root ----
-    // Read-only finds: a path-halving store by one thread could otherwise land
-    // after another thread's root store and leave a non-root parent behind.
-    for (int n = tid; n < total; n += kThreads) sm.P[n] = sfind_ro(sm.P, n, budget, err);
+    if (tid == 0 && sm.nq != 0) atomicOr(err, kErrSmemUnion);
     __syncthreads();
 
     int *tw_ = a.tws + (size_t)tile * g.tile_ints;
