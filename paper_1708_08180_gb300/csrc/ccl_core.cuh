@@ -38,7 +38,7 @@ constexpr int kNodeCap = kThreads * 16;   // at most 16 run starts per 32-bit wo
 constexpr int kBorderCapMax = 576;        // border segments: <= 2*16*NW + 2*NS for every NW
 constexpr int kHdrInts = 4;               // [0] = border-root count
 
-constexpr int kQueueCap = 2048;           // unions left after the local forest pass
+constexpr int kQueueCap = 1024;           // unions left after the local forest pass
 constexpr int kSlotBits = 10;             // border slots per tile < 2^10
 constexpr int kTileBits = 23;             // tiles per image < 2^23
 constexpr long long kMaxTiles = 1ll << kTileBits;
@@ -213,32 +213,25 @@ __device__ __forceinline__ int block_excl_scan(int v, int *warp_sums, int &total
 // not required: links go from the root with the larger key to the one with
 // the smaller key, so every root is the smallest key of its tree).
 
-__device__ __forceinline__ int sfind(volatile int *P, int x, int &budget, int *err) {
+// Parents are 16-bit (a tile has at most kNodeCap = 4096 nodes), so a tile's
+// union-find state stays small enough for 8 blocks per SM.
+typedef unsigned short pnode;
+
+__device__ __forceinline__ int sfind(volatile pnode *P, int x, int &budget, int *err) {
     for (;;) {
         if (--budget < 0) { atomicOr(err, kErrSmemFind); return x; }
         const int p = P[x];
         if (p == x) return x;
         const int g = P[p];
         if (g == p) return p;
-        P[x] = g;   // path halving: g is an ancestor of x (a smaller key)
+        P[x] = (pnode)g;   // path halving: g is an ancestor of x (a smaller key)
         x = g;
     }
 }
 
-// Read-only find, for the pass that stores every node's root: with no
-// path-halving stores, each P[n] ends the pass holding exactly its root.
-__device__ __forceinline__ int sfind_ro(volatile const int *P, int x, int &budget, int *err) {
-    for (;;) {
-        if (--budget < 0) { atomicOr(err, kErrSmemFind); return x; }
-        const int p = P[x];
-        if (p == x) return x;
-        x = p;
-    }
-}
-
-__device__ __forceinline__ void sunion(int *P, const uint16_t *K, int a, int b, int &budget,
+__device__ __forceinline__ void sunion(pnode *P, const uint16_t *K, int a, int b, int &budget,
                                        int *err) {
-    volatile int *vP = P;
+    volatile pnode *vP = P;
     volatile const uint16_t *vK = K;
     for (;;) {
         a = sfind(vP, a, budget, err);
@@ -247,7 +240,7 @@ __device__ __forceinline__ void sunion(int *P, const uint16_t *K, int a, int b, 
         if (budget < 0) { atomicOr(err, kErrSmemUnion); return; }
         if (vK[a] > vK[b]) { int t = a; a = b; b = t; }
         // link root b (larger key) under root a; fails if b stopped being a root
-        if (atomicCAS(&P[b], b, a) == b) return;
+        if (atomicCAS(&P[b], (pnode)b, (pnode)a) == (pnode)b) return;
     }
 }
 

@@ -20,7 +20,7 @@ struct ImageArgs {
 
 // Shared memory of the local-merge phase.
 struct SmemMerge {
-    int P[kNodeCap];               // parent of each segment node
+    pnode P[kNodeCap];             // parent of each segment node
     uint16_t K[kNodeCap];          // key (smallest tile-local pixel index); for a
                                    // root reaching a seam, later its border slot
     uint32_t Q[kQueueCap];         // unions left after the forest pass: a | b << 16
@@ -132,7 +132,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             } else {
                 key = s * TW + 32 * w + i;
             }
-            sm.P[n] = n;
+            sm.P[n] = (pnode)n;
             sm.K[n] = (uint16_t)key;
             ++n;
         }
@@ -165,7 +165,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
                 if (ra == la && rb == lb) return;
                 la = ra;
                 lb = rb;
-                const int old = atomicCAS(&sm.P[rb], rb, ra);
+                const int old = atomicCAS(&sm.P[rb], (pnode)rb, (pnode)ra);
                 if (old != rb && old != ra) {
                     const int q = atomicAdd(&sm.nq, 1);
                     if (q < kQueueCap) sm.Q[q] = (uint32_t)ra | ((uint32_t)old << 16);
@@ -204,14 +204,17 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     }
     __syncthreads();
     // (2) pointer jumping until every node points at its tree's root
-    volatile int *vP = sm.P;
+    volatile pnode *vP = sm.P;
+    // Plain loads: within a round any mix of old and new parents is valid
+    // (all are ancestors), and the barrier between rounds publishes the stores.
     auto jump = [&]() {
         for (int round = 0; round < 64; ++round) {
             int changed = 0;
+#pragma unroll 4
             for (int n = tid; n < total; n += kThreads) {
-                const int p = vP[n];
-                const int gp = vP[p];
-                if (gp != p) { vP[n] = gp; changed = 1; }
+                const int p = sm.P[n];
+                const int gp = sm.P[p];
+                if (gp != p) { sm.P[n] = (pnode)gp; changed = 1; }
             }
             if (!__syncthreads_or(changed)) return;
         }
@@ -242,7 +245,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             int pa = vP[e[k] & 0xFFFFu], pb = vP[e[k] >> 16];
             if (pa == pb) continue;
             if (sm.K[pa] > sm.K[pb]) { const int t = pa; pa = pb; pb = t; }
-            const int old = atomicCAS(&sm.P[pb], pb, pa);   // hook root pb under pa
+            const int old = atomicCAS(&sm.P[pb], (pnode)pb, (pnode)pa);   // hook root pb under pa
             if (old != pb && old != pa) {
                 const int q = atomicAdd(&sm.nq, 1);
                 if (q < kQueueCap) sm.Q[q] = (uint32_t)pa | ((uint32_t)old << 16);
