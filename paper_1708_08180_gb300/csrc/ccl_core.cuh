@@ -38,7 +38,7 @@ constexpr int kNodeCap = kThreads * 16;   // at most 16 run starts per 32-bit wo
 constexpr int kBorderCapMax = 576;        // border segments: <= 2*16*NW + 2*NS for every NW
 constexpr int kHdrInts = 4;               // [0] = border-root count
 
-constexpr int kQueueCap = 1024;           // unions left after the local forest pass
+constexpr int kQueueCap = 2048;           // unions left after the local forest pass
 constexpr int kSlotBits = 10;             // border slots per tile < 2^10
 constexpr int kTileBits = 23;             // tiles per image < 2^23
 constexpr long long kMaxTiles = 1ll << kTileBits;
@@ -213,9 +213,9 @@ __device__ __forceinline__ int block_excl_scan(int v, int *warp_sums, int &total
 // not required: links go from the root with the larger key to the one with
 // the smaller key, so every root is the smallest key of its tree).
 
-// Parents are 16-bit (a tile has at most kNodeCap = 4096 nodes), so a tile's
-// union-find state stays small enough for 8 blocks per SM.
-typedef unsigned short pnode;
+// Parents are plain 32-bit ints: shared-memory compare-and-swap is native at
+// that width.
+typedef int pnode;
 
 __device__ __forceinline__ int sfind(volatile pnode *P, int x, int &budget, int *err) {
     for (;;) {
