@@ -298,11 +298,48 @@ __device__ __forceinline__ gnode gfind(const GlobalForest &F, gnode x, int &budg
     return r;
 }
 
+// Both finds of a union, walked in lock step so their loads overlap (the
+// latency is the longer walk, not the sum); same compression rule as gfind.
+__device__ __forceinline__ void gfind2(const GlobalForest &F, gnode &a, gnode &b, int &budget,
+                                       int *err) {
+    gnode ra = a, rb = b;
+    gnode prev_a = kNoNode, prev_b = kNoNode, wa = kNoNode, wb = kNoNode;
+    bool da = false, db = false;
+    while (!(da && db)) {
+        if (--budget < 0) { atomicOr(err, kErrGlobFind); a = ra; b = rb; return; }
+        const gnode pa = da ? ra : __ldcg(F.par(ra));
+        const gnode pb = db ? rb : __ldcg(F.par(rb));
+        if (!da) {
+            if (pa == ra) {
+                da = true;
+            } else {
+                if (prev_a != kNoNode && wa == kNoNode) wa = prev_a;
+                prev_a = ra;
+                ra = pa;
+            }
+        }
+        if (!db) {
+            if (pb == rb) {
+                db = true;
+            } else {
+                if (prev_b != kNoNode && wb == kNoNode) wb = prev_b;
+                prev_b = rb;
+                rb = pb;
+            }
+        }
+    }
+    // a node seen below its root has a larger key than that root: the new
+    // link cannot close a cycle
+    if (wa != kNoNode) __stcg(F.par(wa), ra);
+    if (wb != kNoNode) __stcg(F.par(wb), rb);
+    a = ra;
+    b = rb;
+}
+
 __device__ __forceinline__ void gunion(const GlobalForest &F, gnode a, gnode b, int &budget,
                                        int *err) {
     for (;;) {
-        a = gfind(F, a, budget, err);
-        b = gfind(F, b, budget, err);
+        gfind2(F, a, b, budget, err);
         if (a == b) return;
         if (budget < 0) { atomicOr(err, kErrGlobUnion); return; }
         if (a > b) { const gnode t = a; a = b; b = t; }

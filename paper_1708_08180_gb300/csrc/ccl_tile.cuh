@@ -394,160 +394,171 @@ struct SmemSeams {
     gnode list[kThreads / 32][kSeamList][2];
 };
 
-// Per-lane pair generator for item `idx` (horizontal: one 32-pixel word of a
-// seam row pair; vertical: one strip of a vertical seam).  next() yields the
-// item's pairs one at a time (consecutive repeats dropped) and false when done.
-struct SeamPairs {
-    // horizontal state
-    uint32_t os = 0, dr = 0, dl = 0;
-    int xw = 0;
-    const long long *up = nullptr, *dn = nullptr;   // record rows of tile (row, column 0)
-    int tile_ints = 0, log2tw = 0, twm = 0;
-    // vertical state: up to three candidate pairs
-    int nv = 0, vi = 0;
-    gnode va0 = 0, vb0 = 0, va1 = 0, vb1 = 0, va2 = 0, vb2 = 0;
-    gnode la = ~0ull, lb = ~0ull;
-    bool bad = false;   // a seam record without a slot was met
-
-    __device__ __forceinline__ void push(gnode ka, gnode kb) {
-        if (nv == 0) { va0 = ka; vb0 = kb; } else if (nv == 1) { va1 = ka; vb1 = kb; } else { va2 = ka; vb2 = kb; }
-        ++nv;
+// Warp step of the seam dedup: every lane offers (have, ka, kb); lanes with
+// equal pairs elect their lowest lane, which appends the pair to the warp's
+// list (slots from a ballot, no atomics).  All 32 lanes must call it.
+__device__ __forceinline__ void seam_offer(bool have, gnode ka, gnode kb, gnode (*list)[2], int &n,
+                                           const GlobalForest &F, int &budget, int *err) {
+    const int lane = threadIdx.x & 31;
+    // pairs are identified by (a, b) folded into 64 bits; equal keys are
+    // equal pairs or (rarely) a collision, which only skips a duplicate of a
+    // pair some lane still unions
+    const unsigned long long key = have ? (ka * 0x9E3779B97F4A7C15ull) ^ kb : ~0ull;
+    const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
+    const int first = __ffs(same) - 1;
+    const bool leader = have && first == lane;
+    const gnode fa = __shfl_sync(0xFFFFFFFFu, ka, first);
+    const gnode fb = __shfl_sync(0xFFFFFFFFu, kb, first);
+    const unsigned lead = __ballot_sync(0xFFFFFFFFu, leader);
+    // a lane whose pair differs from its leader's (a folded-key collision)
+    // unions on its own
+    if (have && !leader && (fa != ka || fb != kb)) gunion(F, ka, kb, budget, err);
+    if (leader) {
+        const int slot = n + __popc(lead & ((1u << lane) - 1u));
+        if (slot < kSeamList) { list[slot][0] = ka; list[slot][1] = kb; }
+        else gunion(F, ka, kb, budget, err);   // list full: union now
     }
-
-    // node of the record at global column xg in the tile row starting at tile t0
-    // (kNoNode if the record holds no node, which valid data never does)
-    __device__ __forceinline__ gnode rec(const long long *b, int xg) const {
-        return (gnode)__ldcg(b + (size_t)(xg >> log2tw) * (tile_ints / 2) + (xg & twm));
-    }
-    __device__ __forceinline__ bool next(gnode &ka, gnode &kb) {
-        for (;;) {
-            if (os) {
-                const int x = __ffs(os) - 1; os &= os - 1;
-                ka = rec(up, xw + x); kb = rec(dn, xw + x);
-            } else if (dr) {
-                const int x = __ffs(dr) - 1; dr &= dr - 1;
-                ka = rec(up, xw + x - 1); kb = rec(dn, xw + x);
-            } else if (dl) {
-                const int x = __ffs(dl) - 1; dl &= dl - 1;
-                ka = rec(up, xw + x + 1); kb = rec(dn, xw + x);
-            } else if (vi < nv) {
-                ka = vi == 0 ? va0 : vi == 1 ? va1 : va2;
-                kb = vi == 0 ? vb0 : vi == 1 ? vb1 : vb2;
-                ++vi;
-            } else {
-                return false;
-            }
-            if (ka == kNoNode || kb == kNoNode) { bad = true; continue; }
-            if (ka != la || kb != lb) { la = ka; lb = kb; return true; }
-        }
-    }
-};
-
-__device__ __forceinline__ void seam_pairs_init(const ImageArgs &a, long long idx,
-                                                long long nitems, SeamPairs &sp) {
-    const Geom &g = a.g;
-    const long long nh_real = seam_h_real(g);
-    const long long nh = seam_h_items(g);
-    if (idx < nh) {
-        if (idx >= nh_real) return;
-        const long long per_row = (long long)g.nwg * kSeamGroupsPerWord;
-        const int ty = (int)(idx / per_row) + 1;
-        const int grp = (int)(idx % per_row);
-        const int j = grp / kSeamGroupsPerWord;
-        const uint32_t gmask = 0xFFu << (8 * (grp % kSeamGroupsPerWord));
-        const int y = ty * g.th;
-        const uint32_t *ra_ = a.bits + (size_t)(y - 1) * g.nwg;
-        const uint32_t *rb_ = a.bits + (size_t)y * g.nwg;
-        const uint32_t av = __ldcg(ra_ + j), bv = __ldcg(rb_ + j);
-        if (!(bv & gmask)) return;   // every contact needs a pixel of row y in the group
-        const uint32_t aL = j > 0 ? (__ldcg(ra_ + j - 1) >> 31) : 0u;
-        const uint32_t bL = j > 0 ? (__ldcg(rb_ + j - 1) >> 31) : 0u;
-        const uint32_t aR = j < g.nwg - 1 ? (__ldcg(ra_ + j + 1) & 1u) : 0u;
-        const uint32_t bR = j < g.nwg - 1 ? (__ldcg(rb_ + j + 1) & 1u) : 0u;
-        sp.up = reinterpret_cast<const long long *>(
-                    a.tws + (size_t)(ty - 1) * g.tiles_x * g.tile_ints + g.off_rec) + g.tw;
-        sp.dn = reinterpret_cast<const long long *>(
-                    a.tws + (size_t)ty * g.tiles_x * g.tile_ints + g.off_rec);
-        sp.tile_ints = g.tile_ints;
-        sp.log2tw = g.log2tw;
-        sp.twm = g.tw - 1;
-        sp.xw = 32 * j;
-        const uint32_t o = av & bv;
-        sp.os = o & ~((o << 1) | (aL & bL)) & gmask;
-        if (g.hs == 2) {
-            sp.dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL) & gmask;
-            sp.dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31)) & gmask;
-        }
-        return;
-    }
-    if (idx >= nitems) return;
-    const long long v = idx - nh;
-    const int s = (int)(v % g.ns);
-    const long long t = v / g.ns;
-    const int ty = (int)(t % g.tiles_y);
-    const int tx = (int)(t / g.tiles_y) + 1;
-    const int x = tx * g.tw;
-    const int r0 = ty * g.th + s * g.hs;
-    if (r0 >= g.H) return;
-    const long long tL = (long long)ty * g.tiles_x + (tx - 1), tR = tL + 1;
-    const long long *recL =
-        reinterpret_cast<const long long *>(a.tws + (size_t)tL * g.tile_ints + g.off_rec) + 2 * g.tw + g.ns;
-    const long long *recR =
-        reinterpret_cast<const long long *>(a.tws + (size_t)tR * g.tile_ints + g.off_rec) + 2 * g.tw;
-    auto nL = [&](int ss) { return (gnode)__ldcg(recL + ss); };
-    auto nR = [&](int ss) { return (gnode)__ldcg(recR + ss); };
-    const uint32_t l0 = bit_at(a.bits, g.nwg, r0, x - 1);
-    const uint32_t rr0 = bit_at(a.bits, g.nwg, r0, x);
-    uint32_t l1 = 0, rr1 = 0;
-    if (g.hs == 2 && r0 + 1 < g.H) {
-        l1 = bit_at(a.bits, g.nwg, r0 + 1, x - 1);
-        rr1 = bit_at(a.bits, g.nwg, r0 + 1, x);
-    }
-    if ((l0 | l1) && (rr0 | rr1)) sp.push(nL(s), nR(s));
-    if (g.hs == 2 && s > 0) {
-        // diagonals between the last row of strip s-1 and the first of strip s
-        const uint32_t lu = bit_at(a.bits, g.nwg, r0 - 1, x - 1);
-        const uint32_t ru = bit_at(a.bits, g.nwg, r0 - 1, x);
-        if (lu && rr0) sp.push(nL(s - 1), nR(s));
-        if (l0 && ru) sp.push(nL(s), nR(s - 1));
-    }
+    n += __popc(lead);
 }
 
-// One block of 256 seam items; every lane of every warp must call it.
+// One block of 256 seam items; every lane of every warp must call it.  Items
+// of one warp are all horizontal (8-column groups of a seam row pair) or all
+// vertical (strips of a vertical seam).  Every bit word and seam record an
+// item can need is loaded up front in one round of independent loads; the
+// pairs are then produced from registers.
 __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, long long nitems,
                                            SmemSeams &sm, int *err) {
+    const Geom &g = a.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const GlobalForest F{a.tws, a.g.tile_ints, a.g.off_par};
+    const GlobalForest F{a.tws, g.tile_ints, g.off_par};
     int budget = kGlobHopBudget;
-    SeamPairs sp;
-    seam_pairs_init(a, idx0 + threadIdx.x, nitems, sp);
     gnode(*list)[2] = sm.list[warp];
     int n = 0;   // warp-uniform list length
-    for (;;) {
-        gnode ka = 0, kb = 0;
-        const bool have = sp.next(ka, kb);
-        if (!__any_sync(0xFFFFFFFFu, have)) break;
-        // pairs are identified by (a, b) folded into 64 bits; equal keys are
-        // equal pairs or (rarely) a collision, which only skips a duplicate of
-        // a pair some lane still unions below
-        const unsigned long long key = have ? (ka * 0x9E3779B97F4A7C15ull) ^ kb : ~0ull;
-        const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
-        // the lowest lane of each key group leads; a lane whose pair differs
-        // from its leader's (a collision of the folded key) unions on its own
-        const int first = __ffs(same) - 1;
-        const bool leader = have && first == lane;
-        const gnode fa = __shfl_sync(0xFFFFFFFFu, ka, first);
-        const gnode fb = __shfl_sync(0xFFFFFFFFu, kb, first);
-        const unsigned lead = __ballot_sync(0xFFFFFFFFu, leader);
-        if (have && !leader && (fa != ka || fb != kb)) gunion(F, ka, kb, budget, err);
-        if (leader) {
-            const int slot = n + __popc(lead & ((1u << lane) - 1u));
-            if (slot < kSeamList) { list[slot][0] = ka; list[slot][1] = kb; }
-            else gunion(F, ka, kb, budget, err);   // list full: union now
+    const long long idx = idx0 + threadIdx.x;
+    const long long nh_real = seam_h_real(g);
+    const long long nh = seam_h_items(g);
+    if (idx0 < nh) {
+        // ---- horizontal: 8 columns [c0, c0 + 8) of rows y-1 (a) and y (b) ----
+        uint32_t os = 0, dr = 0, dl = 0;
+        gnode u[10], d[8];   // records of columns c0-1 .. c0+8 above, c0 .. c0+7 below
+#pragma unroll
+        for (int k = 0; k < 10; ++k) u[k] = kNoNode;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) d[k] = kNoNode;
+        if (idx < nh_real) {
+            const long long per_row = (long long)g.nwg * kSeamGroupsPerWord;
+            const int ty = (int)(idx / per_row) + 1;
+            const int grp = (int)(idx % per_row);
+            const int j = grp / kSeamGroupsPerWord;
+            const int sh = 8 * (grp % kSeamGroupsPerWord);
+            const int c0 = 32 * j + sh;
+            const int y = ty * g.th;
+            const uint32_t *ra_ = a.bits + (size_t)(y - 1) * g.nwg;
+            const uint32_t *rb_ = a.bits + (size_t)y * g.nwg;
+            const long long *up = reinterpret_cast<const long long *>(
+                                      a.tws + (size_t)(ty - 1) * g.tiles_x * g.tile_ints + g.off_rec) + g.tw;
+            const long long *dn = reinterpret_cast<const long long *>(
+                                      a.tws + (size_t)ty * g.tiles_x * g.tile_ints + g.off_rec);
+            auto rec = [&](const long long *b, int xg) -> gnode {
+                return (xg >= 0 && xg < g.W)
+                           ? (gnode)__ldcg(b + (size_t)(xg >> g.log2tw) * (g.tile_ints / 2) + (xg & (g.tw - 1)))
+                           : kNoNode;
+            };
+            // one round of independent loads
+            const uint32_t av = __ldcg(ra_ + j), bv = __ldcg(rb_ + j);
+            const uint32_t aW = j > 0 ? __ldcg(ra_ + j - 1) : 0u, bW = j > 0 ? __ldcg(rb_ + j - 1) : 0u;
+            const uint32_t aE = j < g.nwg - 1 ? __ldcg(ra_ + j + 1) : 0u;
+            const uint32_t bE = j < g.nwg - 1 ? __ldcg(rb_ + j + 1) : 0u;
+#pragma unroll
+            for (int k = 0; k < 10; ++k) u[k] = rec(up, c0 - 1 + k);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) d[k] = rec(dn, c0 + k);
+            const uint32_t aL = aW >> 31, bL = bW >> 31, aR = aE & 1u, bR = bE & 1u;
+            const uint32_t o = av & bv;
+            const uint32_t gm = 0xFFu << sh;
+            os = (o & ~((o << 1) | (aL & bL)) & gm) >> sh;
+            if (g.hs == 2) {
+                dr = ((bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL)) & gm) >> sh;
+                dl = ((bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31))) & gm) >> sh;
+            }
         }
-        n += __popc(lead);
+        // two pair slots per column: the overlap or down-right contact, and
+        // the down-left contact; consecutive repeats dropped per lane
+        gnode la = kNoNode, lb = kNoNode;
+        bool bad = false;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+#pragma unroll
+            for (int kind = 0; kind < 2; ++kind) {
+                bool have;
+                gnode ka, kb = d[c];
+                if (kind == 0) {
+                    have = ((os | dr) >> c) & 1u;
+                    ka = ((os >> c) & 1u) ? u[c + 1] : u[c];   // u[c + 1] is column c0 + c
+                } else {
+                    have = (dl >> c) & 1u;
+                    ka = u[c + 2];
+                }
+                if (have && (ka == kNoNode || kb == kNoNode)) { bad = true; have = false; }
+                if (have && ka == la && kb == lb) have = false;
+                if (have) { la = ka; lb = kb; }
+                if (__any_sync(0xFFFFFFFFu, have)) seam_offer(have, ka, kb, list, n, F, budget, err);
+            }
+        }
+        if (bad) atomicOr(err, kErrBorderCap);
+    } else {
+        // ---- vertical: strip s of the seam between tiles tx-1 and tx ----
+        bool h0 = false, h1 = false, h2 = false;
+        gnode kL = kNoNode, kR = kNoNode, kLu = kNoNode, kRu = kNoNode;
+        if (idx < nitems) {
+            const long long v = idx - nh;
+            const int s = (int)(v % g.ns);
+            const long long t = v / g.ns;
+            const int ty = (int)(t % g.tiles_y);
+            const int tx = (int)(t / g.tiles_y) + 1;
+            const int x = tx * g.tw;
+            const int r0 = ty * g.th + s * g.hs;
+            if (r0 < g.H) {
+                const long long tL = (long long)ty * g.tiles_x + (tx - 1), tR = tL + 1;
+                const long long *recL = reinterpret_cast<const long long *>(
+                                            a.tws + (size_t)tL * g.tile_ints + g.off_rec) + 2 * g.tw + g.ns;
+                const long long *recR = reinterpret_cast<const long long *>(
+                                            a.tws + (size_t)tR * g.tile_ints + g.off_rec) + 2 * g.tw;
+                const int wq = x >> 5;   // x is a multiple of 32: column x-1 is bit 31 of word wq-1
+                const uint32_t *row0 = a.bits + (size_t)r0 * g.nwg;
+                const uint32_t A0 = __ldcg(row0 + wq - 1), B0 = __ldcg(row0 + wq);
+                uint32_t A1 = 0, B1 = 0, Au = 0, Bu = 0;
+                if (g.hs == 2 && r0 + 1 < g.H) {
+                    A1 = __ldcg(row0 + g.nwg + wq - 1);
+                    B1 = __ldcg(row0 + g.nwg + wq);
+                }
+                const bool diag = g.hs == 2 && s > 0;
+                if (diag) {
+                    Au = __ldcg(row0 - g.nwg + wq - 1);
+                    Bu = __ldcg(row0 - g.nwg + wq);
+                    kLu = (gnode)__ldcg(recL + s - 1);
+                    kRu = (gnode)__ldcg(recR + s - 1);
+                }
+                kL = (gnode)__ldcg(recL + s);
+                kR = (gnode)__ldcg(recR + s);
+                const uint32_t l0 = A0 >> 31, l1 = A1 >> 31, lu = Au >> 31;
+                const uint32_t rr0 = B0 & 1u, rr1 = B1 & 1u, ru = Bu & 1u;
+                h0 = (l0 | l1) && (rr0 | rr1);
+                // diagonals between the last row of strip s-1 and the first of strip s
+                h1 = diag && lu && rr0;
+                h2 = diag && l0 && ru;
+            }
+        }
+        bool bad = false;
+        auto check = [&](bool &h, gnode p, gnode q) { if (h && (p == kNoNode || q == kNoNode)) { bad = true; h = false; } };
+        check(h0, kL, kR);
+        check(h1, kLu, kR);
+        check(h2, kL, kRu);
+        seam_offer(h0, kL, kR, list, n, F, budget, err);
+        if (__any_sync(0xFFFFFFFFu, h1)) seam_offer(h1, kLu, kR, list, n, F, budget, err);
+        if (__any_sync(0xFFFFFFFFu, h2)) seam_offer(h2, kL, kRu, list, n, F, budget, err);
+        if (bad) atomicOr(err, kErrBorderCap);
     }
-    if (sp.bad) atomicOr(err, kErrBorderCap);
     __syncwarp();
     const int m = n < kSeamList ? n : kSeamList;
     for (int i = lane; i < m; i += 32) gunion(F, list[i][0], list[i][1], budget, err);
