@@ -108,9 +108,9 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             rem &= rem - 1;
             int key;
             if (HS == 2) {
-                // the run from bit i inside this word: adding bit i to m clears
-                // exactly that run (the carry stops at its first zero)
-                const uint32_t part = m & ~(m + (1u << i));
+                // the run from bit i inside this word (len <= 32 - i bits)
+                const int len = __ffsll(~((unsigned long long)m >> i)) - 1;
+                const uint32_t part = (uint32_t)(((1ull << len) - 1ull) << i);
                 const uint32_t tp = top & part;
                 if (tp) {
                     key = (2 * s) * TW + 32 * w + (__ffs(tp) - 1);
@@ -118,7 +118,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
                     // no top-row pixel here: the start's bottom pixel, unless the
                     // segment continues and meets a top-row pixel in a later word
                     key = (2 * s + 1) * TW + 32 * w + i;
-                    if (part >> 31) {   // the run reaches the end of the word
+                    if (i + len == 32) {
                         for (int w2 = w + 1; w2 < NW; ++w2) {
                             const uint32_t t2 = sm.top[tid + (w2 - w)];
                             const uint32_t m2 = t2 | sm.bot[tid + (w2 - w)];
@@ -173,31 +173,32 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
                 }
             };
             const uint32_t o = av & bv;
-            const uint32_t os = o & ~((o << 1) | (aL & bL));
-            uint32_t dr = 0, dl = 0, stA_next0 = 0;
+            uint32_t os = o & ~((o << 1) | (aL & bL));
+            while (os) {
+                const int x = __ffs(os) - 1;
+                os &= os - 1;
+                contact(seg_rank(baseA, stA, x), seg_rank(base, st, x));
+            }
             if (HS == 2) {
                 const uint32_t aR = w < NW - 1 ? (sm.bot[up + 1] & 1u) : 0u;
                 const uint32_t bR = w < NW - 1 ? (sm.top[tid + 1] & 1u) : 0u;
-                stA_next0 = w < NW - 1 ? (sm.st[up + 1] & 1u) : 0u;
+                const uint32_t stA_next0 = w < NW - 1 ? (sm.st[up + 1] & 1u) : 0u;
                 // b-run starts at x right after an a-run that ends at x-1
-                dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
+                uint32_t dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
                 // b-run ends at x right before an a-run that starts at x+1
-                dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31));
-            }
-            // one loop over every column with a contact (a column can hold a
-            // down-right and a down-left contact at once; never an overlap too)
-            uint32_t cm = os | dr | dl;
-            while (cm) {
-                const int x = __ffs(cm) - 1;
-                cm &= cm - 1;
-                const uint32_t bit = 1u << x;
-                const int rb = seg_rank(base, st, x);
-                if (os & bit) contact(seg_rank(baseA, stA, x), rb);
-                if (dr & bit) contact(seg_rank(baseA, stA, x - 1), rb);
-                if (dl & bit)
+                uint32_t dl = bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31));
+                while (dr) {
+                    const int x = __ffs(dr) - 1;
+                    dr &= dr - 1;
+                    contact(seg_rank(baseA, stA, x - 1), seg_rank(base, st, x));
+                }
+                while (dl) {
+                    const int x = __ffs(dl) - 1;
+                    dl &= dl - 1;
                     contact((x == 31) ? (baseA + __popc(stA) + (int)stA_next0 - 1)
                                       : seg_rank(baseA, stA, x + 1),
-                            rb);
+                            seg_rank(base, st, x));
+                }
             }
         }
     }
