@@ -35,8 +35,7 @@ struct BatchHeader {
     int merge_ctr;         // work-queue heads (zero in the staged copy)
     int seam_ctr;
     int link_ctr;
-    int resolve_ctr;
-    int pad[8];
+    int pad[9];
 };
 static_assert(sizeof(BatchHeader) == 64, "header size");
 
@@ -105,24 +104,6 @@ __global__ void __launch_bounds__(256, 2) kb_seams(BatchHeader *hdr, const Batch
         if (c >= total) break;
         const ImageArgs a = imgs[s_img].a;
         seam_block(a, (c - imgs[s_img].chunk_off) * 256, seam_items(a.g), sm, err);
-        __syncthreads();
-    }
-}
-
-// groups of 8 tiles per block, one warp per tile
-__global__ void __launch_bounds__(256) kb_resolve(BatchHeader *hdr, const BatchImage *imgs,
-                                                  int *err) {
-    __shared__ int s_group;
-    const int n = hdr->n, total = hdr->total_tiles;
-    for (;;) {
-        if (threadIdx.x == 0) s_group = atomicAdd(&hdr->resolve_ctr, 1);
-        __syncthreads();
-        const int t = s_group * 8 + (threadIdx.x >> 5);
-        if (s_group * 8 >= total) break;
-        if (t < total) {
-            const int k = find_image_by_tile(imgs, n, t);
-            resolve_tile(imgs[k].a, t - imgs[k].tile_off, threadIdx.x & 31, err);
-        }
         __syncthreads();
     }
 }
@@ -208,7 +189,7 @@ bool plan(const ccl_image *imgs, int n, int conn, Layout &L) {
 }
 
 struct Persist {
-    int merge_blocks = 0, seam_blocks = 0, link_blocks = 0, resolve_blocks = 0;
+    int merge_blocks = 0, seam_blocks = 0, link_blocks = 0;
 };
 
 struct GraphSlot {
@@ -244,13 +225,10 @@ bool persist_dims(int dev, int conn, Persist &p) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, kb_link<1>, kThreads, 0);
     }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, kb_seams, 256, 0);
-    int br = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&br, kb_resolve, 256, 0);
     if (cudaGetLastError() != cudaSuccess) return false;
     p.merge_blocks = sms * (bm > 0 ? bm : 1);
     p.seam_blocks = sms * (bs > 0 ? bs : 1);
     p.link_blocks = sms * (bl > 0 ? bl : 1);
-    p.resolve_blocks = sms * (br > 0 ? br : 1);
     g_persist[dev * 16 + conn] = p;
     return true;
 }
@@ -260,12 +238,10 @@ void launch_kernels(const Persist &p, int conn, BatchHeader *hdr, const BatchIma
     if (conn == 8) {
         kb_merge<2><<<p.merge_blocks, kThreads, 0, s>>>(hdr, imgs, err);
         kb_seams<<<p.seam_blocks, 256, 0, s>>>(hdr, imgs, err);
-        kb_resolve<<<p.resolve_blocks, 256, 0, s>>>(hdr, imgs, err);
         kb_link<2><<<p.link_blocks, kThreads, 0, s>>>(hdr, imgs, err);
     } else {
         kb_merge<1><<<p.merge_blocks, kThreads, 0, s>>>(hdr, imgs, err);
         kb_seams<<<p.seam_blocks, 256, 0, s>>>(hdr, imgs, err);
-        kb_resolve<<<p.resolve_blocks, 256, 0, s>>>(hdr, imgs, err);
         kb_link<1><<<p.link_blocks, kThreads, 0, s>>>(hdr, imgs, err);
     }
 }

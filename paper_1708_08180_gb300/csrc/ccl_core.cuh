@@ -63,9 +63,8 @@ constexpr int kGlobHopBudget = 1 << 20;   // per thread per work item (global me
 // workspace (all offsets in ints from the tile's base):
 //   [0, kHdrInts)               header: [0] = number of border roots
 //   [kHdrInts, off_key)         label of each segment node (node_cap)
-//   [off_key, off_fin)          smallest raster index of each border root's component
+//   [off_key, off_par)          smallest raster index of each border root's component
 //                               inside the tile (border_cap)
-//   [off_fin, off_par)          final label of each border root (resolve pass)
 //   [off_par, off_rec)          parent of each border root in the global forest,
 //                               64-bit node ids (border_cap x 2 ints, 8-byte aligned)
 //   [off_rec, off_rec + rec)    seam records, global node of the position's root
@@ -82,7 +81,7 @@ struct Geom {
     int nwg;        // words per bit-image row = ceil(W / 32)
     int node_cap;   // most segment nodes a tile of this image can hold
     int border_cap; // most border roots
-    int off_key, off_fin, off_par, off_rec, tile_ints;
+    int off_key, off_par, off_rec, tile_ints;
 };
 
 __host__ __device__ inline Geom make_geom(int H, int W, int conn, int tile_w) {
@@ -104,8 +103,7 @@ __host__ __device__ inline Geom make_geom(int H, int W, int conn, int tile_w) {
     g.node_cap = g.ns * per_strip;
     g.border_cap = 2 * per_strip + 2 * g.ns;
     g.off_key = kHdrInts + g.node_cap;
-    g.off_fin = g.off_key + g.border_cap;
-    g.off_par = (g.off_fin + g.border_cap + 1) & ~1;
+    g.off_par = (g.off_key + g.border_cap + 1) & ~1;
     g.off_rec = g.off_par + 2 * g.border_cap;
     g.tile_ints = (g.off_rec + 2 * (2 * g.tw + 2 * g.ns) + 63) & ~63;   // 256-byte multiple
     return g;

@@ -19,11 +19,6 @@ __global__ void __launch_bounds__(256, 2) k_seams(ImageArgs a, long long nitems,
     seam_block(a, (long long)blockIdx.x * 256, nitems, sm, err);
 }
 
-// one warp per tile: final labels of the tile's border roots
-__global__ void __launch_bounds__(256) k_resolve(ImageArgs a, int ntiles, int *err) {
-    const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (tile < ntiles) resolve_tile(a, tile, threadIdx.x & 31, err);
-}
 
 template <int NW, int HS>
 __global__ void __launch_bounds__(kThreads) k_link(ImageArgs a, int *err) {
@@ -140,8 +135,6 @@ ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, in
     if (!local_only && items > 0) {
         const long long blocks = (items + 255) / 256;
         k_seams<<<(unsigned)blocks, 256, 0, stream>>>(a, items, err);
-        const int ntiles = g.tiles_x * g.tiles_y;
-        k_resolve<<<(ntiles + 7) / 8, 256, 0, stream>>>(a, ntiles, err);
     }
     if (timed) cudaEventRecord(t_phase_events[2], stream);
     launch_tile_kernel(a, local_only, err, stream, true);

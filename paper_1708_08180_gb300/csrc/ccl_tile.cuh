@@ -565,23 +565,6 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
 }
 
 // ---------------------------------------------------------------------------
-// Resolve body (end of §II-B): after all seam unions, every border root of
-// tile `tile` finds its global root (compressing the path) and stores its
-// final label, 1 + the root's key.  Run by one warp per tile.
-__device__ __forceinline__ void resolve_tile(const ImageArgs &a, long long tile, int lane,
-                                             int *err) {
-    const GlobalForest F{a.tws, a.g.tile_ints, a.g.off_par};
-    int *tw_ = a.tws + (size_t)tile * a.g.tile_ints;
-    const int nb = min(__ldcg(tw_), a.g.border_cap);
-    int budget = kGlobHopBudget;
-    const gnode *par = reinterpret_cast<const gnode *>(tw_ + a.g.off_par);
-    for (int j = lane; j < nb; j += 32) {
-        const gnode r = gfind(F, __ldcg(par + j), budget, err);
-        tw_[a.g.off_fin + j] = 1 + gnode_key(r);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Link body (§II-C): re-derive the segments of the tile from the bit image,
 // give every segment its final label (its local root's, or the resolved label
 // of its border root), and write one int32 per pixel.  The stores are laid
@@ -611,7 +594,23 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
     const uint32_t st = m & ~((m << 1) | mL);
     const int *tw_ = a.tws + (size_t)tile * g.tile_ints;
     const int nb = min(__ldcg(tw_), g.border_cap);
-    for (int j = tid; j < nb; j += kThreads) sm.R[j] = __ldcg(tw_ + g.off_fin + j);
+    // final label of each border root: 1 + the key of its global root (the
+    // seam unions are complete; a read-only walk, usually one or two hops)
+    {
+        const GlobalForest F{a.tws, g.tile_ints, g.off_par};
+        const gnode *par = reinterpret_cast<const gnode *>(tw_ + g.off_par);
+        int budget = kGlobHopBudget;
+        for (int j = tid; j < nb; j += kThreads) {
+            gnode r = __ldcg(par + j);
+            for (;;) {
+                if (--budget < 0) { atomicOr(err, kErrGlobFind); break; }
+                const gnode p = __ldcg(F.par(r));
+                if (p == r) break;
+                r = p;
+            }
+            sm.R[j] = 1 + gnode_key(r);
+        }
+    }
     int total;
     const int base = block_excl_scan(__popc(st), sm.warp_sums, total);   // syncs: R visible
     sm.st[tid] = st;
