@@ -380,52 +380,48 @@ __host__ __device__ inline long long seam_items(const Geom &g) {
     return seam_h_items(g) + (long long)(g.tiles_x - 1) * g.tiles_y * g.ns;
 }
 
-// Seam unions of one block of 256 items, warp by warp.  Each round every lane
-// offers its next pair (local root above/left, local root below/right); lanes
-// holding equal pairs elect one leader (__match_any_sync), and leaders append
-// their pair to the warp's list (slots from a ballot, no atomics).  One
-// component crossing a seam many times yields the same pair over and over, so
-// the lists stay short.  Then the warp's lanes run the listed unions in
-// parallel: a warp costs about one union's chain of dependent global loads
-// instead of one per contact.
+// Seam unions of one block of 256 items, warp by warp.  Each lane lists the
+// pairs (local root above/left, local root below/right) of its item's
+// contacts, dropping a pair equal to its previous one and a first pair equal
+// to the previous lane's last; one warp scan packs all lanes' pairs into the
+// warp's list.  The list is then deduplicated 32 entries at a time
+// (__match_any_sync; the first of equal pairs is kept, in place), and the
+// lanes run the remaining unions in parallel.  One component crossing a seam
+// many times yields the same pair over and over, so a warp costs about one
+// union's chain of dependent global loads instead of one per contact.
 constexpr int kSeamList = 128;   // pairs per warp before falling back to direct unions
 
 struct SmemSeams {
     gnode list[kThreads / 32][kSeamList][2];
 };
 
-// Warp step of the seam dedup: every lane offers (have, ka, kb); lanes with
-// equal pairs elect their lowest lane, which appends the pair to the warp's
-// list (slots from a ballot, no atomics).  All 32 lanes must call it.
-__device__ __forceinline__ void seam_offer(bool have, gnode ka, gnode kb, gnode (*list)[2], int &n,
-                                           const GlobalForest &F, int &budget, int *err) {
+// Warp-wide exclusive scan of c; `total` gets the warp's sum.
+__device__ __forceinline__ int warp_excl_scan(int c, int &total) {
     const int lane = threadIdx.x & 31;
-    // pairs are identified by (a, b) folded into 64 bits; equal keys are
-    // equal pairs or (rarely) a collision, which only skips a duplicate of a
-    // pair some lane still unions
-    const unsigned long long key = have ? (ka * 0x9E3779B97F4A7C15ull) ^ kb : ~0ull;
-    const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
-    const int first = __ffs(same) - 1;
-    const bool leader = have && first == lane;
-    const gnode fa = __shfl_sync(0xFFFFFFFFu, ka, first);
-    const gnode fb = __shfl_sync(0xFFFFFFFFu, kb, first);
-    const unsigned lead = __ballot_sync(0xFFFFFFFFu, leader);
-    // a lane whose pair differs from its leader's (a folded-key collision)
-    // unions on its own
-    if (have && !leader && (fa != ka || fb != kb)) gunion(F, ka, kb, budget, err);
-    if (leader) {
-        const int slot = n + __popc(lead & ((1u << lane) - 1u));
-        if (slot < kSeamList) { list[slot][0] = ka; list[slot][1] = kb; }
-        else gunion(F, ka, kb, budget, err);   // list full: union now
+    int x = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= d) x += y;
     }
-    n += __popc(lead);
+    total = __shfl_sync(0xFFFFFFFFu, x, 31);
+    return x - c;
+}
+
+// Drops the lane's first kept pair (lowest bit of `keep`) when it equals the
+// previous lane's last kept pair (la, lb); the previous lane's pair, or one
+// equal to it further left, stays listed.
+__device__ __forceinline__ uint32_t drop_left_repeat(uint32_t keep, gnode fa, gnode fb, gnode la,
+                                                     gnode lb) {
+    const gnode pa = __shfl_up_sync(0xFFFFFFFFu, la, 1);
+    const gnode pb = __shfl_up_sync(0xFFFFFFFFu, lb, 1);
+    if ((threadIdx.x & 31) > 0 && keep && fa == pa && fb == pb) keep &= keep - 1u;
+    return keep;
 }
 
 // One block of 256 seam items; every lane of every warp must call it.  Items
 // of one warp are all horizontal (8-column groups of a seam row pair) or all
-// vertical (strips of a vertical seam).  Every bit word and seam record an
-// item can need is loaded up front in one round of independent loads; the
-// pairs are then produced from registers.
+// vertical (strips of a column seam).
 __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, long long nitems,
                                            SmemSeams &sm, int *err) {
     const Geom &g = a.g;
@@ -437,6 +433,7 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
     const long long idx = idx0 + threadIdx.x;
     const long long nh_real = seam_h_real(g);
     const long long nh = seam_h_items(g);
+    bool bad = false;   // a contact without a record: a border root was dropped
     if (idx0 < nh) {
         // ---- horizontal: 8 columns [c0, c0 + 8) of rows y-1 (a) and y (b) ----
         uint32_t os = 0, dr = 0, dl = 0;
@@ -482,30 +479,46 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
                 dl = ((bv & ~av & ~((bv >> 1) | (bR << 31)) & ((av >> 1) | (aR << 31))) & gm) >> sh;
             }
         }
-        // two pair slots per column: the overlap or down-right contact, and
-        // the down-left contact; consecutive repeats dropped per lane
-        gnode la = kNoNode, lb = kNoNode;
-        bool bad = false;
+        // two pair slots per column, bit 2c + kind of `keep`: kind 0 is the
+        // overlap or down-right contact at column c0 + c, kind 1 the down-left
+        auto pair_of = [&](int c, int kind, gnode &ka, gnode &kb) {
+            kb = d[c];
+            ka = kind == 0 ? (((os >> c) & 1u) ? u[c + 1] : u[c]) : u[c + 2];
+        };
+        uint32_t keep = 0u;
+        gnode fa = kNoNode, fb = kNoNode, la = kNoNode, lb = kNoNode;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
 #pragma unroll
             for (int kind = 0; kind < 2; ++kind) {
-                bool have;
-                gnode ka, kb = d[c];
-                if (kind == 0) {
-                    have = ((os | dr) >> c) & 1u;
-                    ka = ((os >> c) & 1u) ? u[c + 1] : u[c];   // u[c + 1] is column c0 + c
-                } else {
-                    have = (dl >> c) & 1u;
-                    ka = u[c + 2];
-                }
+                bool have = kind == 0 ? (((os | dr) >> c) & 1u) : ((dl >> c) & 1u);
+                gnode ka, kb;
+                pair_of(c, kind, ka, kb);
                 if (have && (ka == kNoNode || kb == kNoNode)) { bad = true; have = false; }
                 if (have && ka == la && kb == lb) have = false;
-                if (have) { la = ka; lb = kb; }
-                if (__any_sync(0xFFFFFFFFu, have)) seam_offer(have, ka, kb, list, n, F, budget, err);
+                if (have) {
+                    if (keep == 0u) { fa = ka; fb = kb; }
+                    la = ka;
+                    lb = kb;
+                    keep |= 1u << (2 * c + kind);
+                }
             }
         }
-        if (bad) atomicOr(err, kErrBorderCap);
+        keep = drop_left_repeat(keep, fa, fb, la, lb);
+        int slot = warp_excl_scan(__popc(keep), n);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+#pragma unroll
+            for (int kind = 0; kind < 2; ++kind) {
+                if ((keep >> (2 * c + kind)) & 1u) {
+                    gnode ka, kb;
+                    pair_of(c, kind, ka, kb);
+                    if (slot < kSeamList) { list[slot][0] = ka; list[slot][1] = kb; }
+                    else gunion(F, ka, kb, budget, err);   // list full: union now
+                    ++slot;
+                }
+            }
+        }
     } else {
         // ---- vertical: strip s of the seam between tiles tx-1 and tx ----
         bool h0 = false, h1 = false, h2 = false;
@@ -549,19 +562,70 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
                 h2 = diag && l0 && ru;
             }
         }
-        bool bad = false;
-        auto check = [&](bool &h, gnode p, gnode q) { if (h && (p == kNoNode || q == kNoNode)) { bad = true; h = false; } };
-        check(h0, kL, kR);
-        check(h1, kLu, kR);
-        check(h2, kL, kRu);
-        seam_offer(h0, kL, kR, list, n, F, budget, err);
-        if (__any_sync(0xFFFFFFFFu, h1)) seam_offer(h1, kLu, kR, list, n, F, budget, err);
-        if (__any_sync(0xFFFFFFFFu, h2)) seam_offer(h2, kL, kRu, list, n, F, budget, err);
-        if (bad) atomicOr(err, kErrBorderCap);
+        // pair k: 0 = (kLu, kR), 1 = (kL, kRu), 2 = (kL, kR), in this order
+        auto pair_of = [&](int k, gnode &ka, gnode &kb) {
+            ka = k == 0 ? kLu : kL;
+            kb = k == 1 ? kRu : kR;
+        };
+        uint32_t keep = 0u;
+        gnode fa = kNoNode, fb = kNoNode, la = kNoNode, lb = kNoNode;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            bool have = k == 0 ? h1 : (k == 1 ? h2 : h0);
+            gnode ka, kb;
+            pair_of(k, ka, kb);
+            if (have && (ka == kNoNode || kb == kNoNode)) { bad = true; have = false; }
+            if (have && ka == la && kb == lb) have = false;
+            if (have) {
+                if (keep == 0u) { fa = ka; fb = kb; }
+                la = ka;
+                lb = kb;
+                keep |= 1u << k;
+            }
+        }
+        keep = drop_left_repeat(keep, fa, fb, la, lb);
+        int slot = warp_excl_scan(__popc(keep), n);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if ((keep >> k) & 1u) {
+                gnode ka, kb;
+                pair_of(k, ka, kb);
+                if (slot < kSeamList) { list[slot][0] = ka; list[slot][1] = kb; }
+                else gunion(F, ka, kb, budget, err);   // list full: union now
+                ++slot;
+            }
+        }
+    }
+    if (bad) atomicOr(err, kErrBorderCap);
+    __syncwarp();
+    // deduplicate the list 32 entries at a time, in place: of equal pairs
+    // within a chunk the lowest lane's stays.  Pairs are compared folded into
+    // 64 bits; a lane whose pair differs from its elected lane's (a
+    // collision) stays too.
+    const int m = n < kSeamList ? n : kSeamList;
+    int nu = 0;   // warp-uniform count of kept pairs
+    for (int i0 = 0; i0 < m; i0 += 32) {
+        const int i = i0 + lane;
+        const bool have = i < m;
+        const gnode ka = have ? list[i][0] : kNoNode;
+        const gnode kb = have ? list[i][1] : kNoNode;
+        const unsigned long long key = have ? (ka * 0x9E3779B97F4A7C15ull) ^ kb : ~0ull;
+        const unsigned same = __match_any_sync(0xFFFFFFFFu, key);
+        const int first = __ffs(same) - 1;
+        const gnode ea = __shfl_sync(0xFFFFFFFFu, ka, first);
+        const gnode eb = __shfl_sync(0xFFFFFFFFu, kb, first);
+        const bool keepit = have && (first == lane || ea != ka || eb != kb);
+        const unsigned km = __ballot_sync(0xFFFFFFFFu, keepit);
+        __syncwarp();   // every lane has read its entry before any is overwritten
+        if (keepit) {
+            const int o = nu + __popc(km & ((1u << lane) - 1u));   // o <= i
+            list[o][0] = ka;
+            list[o][1] = kb;
+        }
+        nu += __popc(km);
     }
     __syncwarp();
-    const int m = n < kSeamList ? n : kSeamList;
-    for (int i = lane; i < m; i += 32) gunion(F, list[i][0], list[i][1], budget, err);
+    for (int i = lane; i < nu; i += 32) gunion(F, list[i][0], list[i][1], budget, err);
 }
 
 // ---------------------------------------------------------------------------
