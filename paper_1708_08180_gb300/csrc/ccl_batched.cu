@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) kb_merge(BatchHeader *hdr, const Bat
     }
 }
 
-__global__ void __launch_bounds__(256, 3) kb_seams(BatchHeader *hdr, const BatchImage *imgs,
+__global__ void __launch_bounds__(256, 4) kb_seams(BatchHeader *hdr, const BatchImage *imgs,
                                                 int *err) {
     __shared__ SmemSeams sm;
     __shared__ long long s_chunk;

@@ -14,7 +14,7 @@ __global__ void __launch_bounds__(kThreads) k_merge(ImageArgs a, int local_only,
     merge_tile<NW, HS>(a, blockIdx.x, local_only != 0, sm, err);
 }
 
-__global__ void __launch_bounds__(256, 3) k_seams(ImageArgs a, long long nitems, int *err) {
+__global__ void __launch_bounds__(256, 4) k_seams(ImageArgs a, long long nitems, int *err) {
     __shared__ SmemSeams sm;
     seam_block(a, (long long)blockIdx.x * 256, nitems, sm, err);
 }

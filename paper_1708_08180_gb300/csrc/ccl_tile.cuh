@@ -353,20 +353,22 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
 }
 
 // ---------------------------------------------------------------------------
-// Kernel 2 body: seam unions (§II-B).  Work items: 8-column groups of the
-// horizontal seams (rows y-1, y with y = ty*TH), (tiles_y-1)*nwg*4 of them,
+// Kernel 2 body: seam unions (§II-B).  Work items: 4-column groups of the
+// horizontal seams (rows y-1, y with y = ty*TH), (tiles_y-1)*nwg*8 of them,
 // padded to a multiple of 256 so that no warp or 256-item chunk mixes the two
 // kinds; then
 // one item per strip of each vertical seam, (tiles_x-1)*tiles_y*NS.  Each
 // touching pair of runs across a seam yields one union of the two local roots
-// (deduplicated per block of 256 items, see seam_block).
+// (deduplicated per warp, see seam_block).
 __device__ __forceinline__ uint32_t bit_at(const uint32_t *bits, int nwg, int y, int x) {
     return (__ldcg(bits + (size_t)y * nwg + (x >> 5)) >> (x & 31)) & 1u;
 }
 
-// horizontal seam items cover 8 columns each (4 per 32-bit word): about two
-// contacts per thread at p = 0.5, so a warp waits on few dependent loads
-constexpr int kSeamGroupsPerWord = 4;
+// horizontal seam items cover kGroupCols = 4 columns each (8 per 32-bit
+// word): about one contact per thread at p = 0.5, and few enough live
+// records (6 above, 4 below) that the kernel holds 4 blocks per SM
+constexpr int kSeamGroupsPerWord = 8;
+constexpr int kGroupCols = 32 / kSeamGroupsPerWord;
 
 __host__ __device__ inline long long seam_h_real(const Geom &g) {
     return (long long)(g.tiles_y - 1) * g.nwg * kSeamGroupsPerWord;
@@ -420,7 +422,7 @@ __device__ __forceinline__ uint32_t drop_left_repeat(uint32_t keep, gnode fa, gn
 }
 
 // One block of 256 seam items; every lane of every warp must call it.  Items
-// of one warp are all horizontal (8-column groups of a seam row pair) or all
+// of one warp are all horizontal (4-column groups of a seam row pair) or all
 // vertical (strips of a column seam).
 __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, long long nitems,
                                            SmemSeams &sm, int *err) {
@@ -435,19 +437,20 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
     const long long nh = seam_h_items(g);
     bool bad = false;   // a contact without a record: a border root was dropped
     if (idx0 < nh) {
-        // ---- horizontal: 8 columns [c0, c0 + 8) of rows y-1 (a) and y (b) ----
+        // ---- horizontal: columns [c0, c0 + kGroupCols) of rows y-1 (a) and y (b) ----
+        constexpr int GC = kGroupCols;
         uint32_t os = 0, dr = 0, dl = 0;
-        gnode u[10], d[8];   // records of columns c0-1 .. c0+8 above, c0 .. c0+7 below
+        gnode u[GC + 2], d[GC];   // records of columns c0-1 .. c0+GC above, c0 .. c0+GC-1 below
 #pragma unroll
-        for (int k = 0; k < 10; ++k) u[k] = kNoNode;
+        for (int k = 0; k < GC + 2; ++k) u[k] = kNoNode;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) d[k] = kNoNode;
+        for (int k = 0; k < GC; ++k) d[k] = kNoNode;
         if (idx < nh_real) {
             const long long per_row = (long long)g.nwg * kSeamGroupsPerWord;
             const int ty = (int)(idx / per_row) + 1;
             const int grp = (int)(idx % per_row);
             const int j = grp / kSeamGroupsPerWord;
-            const int sh = 8 * (grp % kSeamGroupsPerWord);
+            const int sh = GC * (grp % kSeamGroupsPerWord);
             const int c0 = 32 * j + sh;
             const int y = ty * g.th;
             const uint32_t *ra_ = a.bits + (size_t)(y - 1) * g.nwg;
@@ -467,12 +470,12 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
             const uint32_t aE = j < g.nwg - 1 ? __ldcg(ra_ + j + 1) : 0u;
             const uint32_t bE = j < g.nwg - 1 ? __ldcg(rb_ + j + 1) : 0u;
 #pragma unroll
-            for (int k = 0; k < 10; ++k) u[k] = rec(up, c0 - 1 + k);
+            for (int k = 0; k < GC + 2; ++k) u[k] = rec(up, c0 - 1 + k);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) d[k] = rec(dn, c0 + k);
+            for (int k = 0; k < GC; ++k) d[k] = rec(dn, c0 + k);
             const uint32_t aL = aW >> 31, bL = bW >> 31, aR = aE & 1u, bR = bE & 1u;
             const uint32_t o = av & bv;
-            const uint32_t gm = 0xFFu << sh;
+            const uint32_t gm = ((1u << GC) - 1u) << sh;
             os = (o & ~((o << 1) | (aL & bL)) & gm) >> sh;
             if (g.hs == 2) {
                 dr = ((bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL)) & gm) >> sh;
@@ -488,7 +491,7 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
         uint32_t keep = 0u;
         gnode fa = kNoNode, fb = kNoNode, la = kNoNode, lb = kNoNode;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < GC; ++c) {
 #pragma unroll
             for (int kind = 0; kind < 2; ++kind) {
                 bool have = kind == 0 ? (((os | dr) >> c) & 1u) : ((dl >> c) & 1u);
@@ -507,7 +510,7 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
         keep = drop_left_repeat(keep, fa, fb, la, lb);
         int slot = warp_excl_scan(__popc(keep), n);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < GC; ++c) {
 #pragma unroll
             for (int kind = 0; kind < 2; ++kind) {
                 if ((keep >> (2 * c + kind)) & 1u) {
