@@ -124,6 +124,18 @@ __host__ __device__ inline size_t tiles_bytes(const Geom &g) {
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch (sm_90 and later).  A grid launched with
+// programmatic stream serialisation may start once every block of the grid
+// before it on the stream has called pdl_launch_dependents() (or exited);
+// pdl_wait() then blocks until that previous grid has completed and its
+// memory writes are visible.  For a grid launched without the attribute both
+// are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // bit helpers
 
 // mask of bits 0..x (x in [-1, 31]); x = -1 gives 0

@@ -2,20 +2,31 @@
 // unions, link) and the ccl_label / ccl_label_tiled entry points.
 #include <atomic>
 #include <mutex>
+#include <utility>
 
 #include "ccl_internal.h"
 #include "ccl_tile.cuh"
 
 namespace ccl {
 
+// The link kernel is launched with programmatic stream serialisation: once
+// every seam block has started (and passed its own wait), link blocks may
+// start and run the part of their prologue that reads only the local-merge
+// output, then wait (pdl_wait in link_tile) for the seam unions.  When the
+// local merge fits in one wave of blocks the seam kernel is launched the
+// same way, so that its launch overlaps the local merge's last blocks; its
+// blocks wait for the local merge before reading anything.
 template <int NW, int HS>
 __global__ void __launch_bounds__(kThreads) k_merge(ImageArgs a, int local_only, int *err) {
     __shared__ SmemMerge sm;
+    pdl_launch_dependents();
     merge_tile<NW, HS>(a, blockIdx.x, local_only != 0, sm, err);
 }
 
 __global__ void __launch_bounds__(256, 4) k_seams(ImageArgs a, long long nitems, int *err) {
     __shared__ SmemSeams sm;
+    pdl_wait();
+    pdl_launch_dependents();
     seam_block(a, (long long)blockIdx.x * 256, nitems, sm, err);
 }
 
@@ -26,21 +37,61 @@ __global__ void __launch_bounds__(kThreads, 8) k_link(ImageArgs a, int *err) {
     link_tile<NW, HS>(a, blockIdx.x, sm, err);
 }
 
+// local-merge blocks resident per SM (shared memory: 6 x SmemMerge)
+constexpr int kMergeBlocksPerSm = 6;
+
+// SMs of the current device (cached per device)
+static int sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return 0; }
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
+// launch with programmatic stream serialisation (see k_merge)
+template <typename... P, typename... A>
+static cudaError_t launch_pdl(void (*kernel)(P...), unsigned grid, unsigned block, cudaStream_t s,
+                              A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
+// link_early: the link kernel directly follows the seam kernel and may start
+// early; otherwise (no seam kernel ran) it waits for the local merge as usual
 template <int NW, int HS>
 static void launch_merge_link(const ImageArgs &a, bool local_only, int *err, cudaStream_t s,
-                              bool link) {
+                              bool link, bool link_early) {
     const int ntiles = a.g.tiles_x * a.g.tiles_y;
     if (!link)
         k_merge<NW, HS><<<ntiles, kThreads, 0, s>>>(a, local_only ? 1 : 0, err);
+    else if (link_early)
+        launch_pdl(k_link<NW, HS>, (unsigned)ntiles, (unsigned)kThreads, s, a, err);
     else
         k_link<NW, HS><<<ntiles, kThreads, 0, s>>>(a, err);
 }
 
 static void launch_tile_kernel(const ImageArgs &a, bool local_only, int *err, cudaStream_t s,
-                               bool link) {
+                               bool link, bool link_early = false) {
     const int nw = a.g.nw, hs = a.g.hs;
 #define CCL_CASE(NW_, HS_) \
-    if (nw == NW_ && hs == HS_) { launch_merge_link<NW_, HS_>(a, local_only, err, s, link); return; }
+    if (nw == NW_ && hs == HS_) { launch_merge_link<NW_, HS_>(a, local_only, err, s, link, link_early); return; }
     CCL_CASE(1, 1) CCL_CASE(2, 1) CCL_CASE(4, 1) CCL_CASE(8, 1)
     CCL_CASE(1, 2) CCL_CASE(2, 2) CCL_CASE(4, 2) CCL_CASE(8, 2)
 #undef CCL_CASE
@@ -132,12 +183,16 @@ ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, in
     launch_tile_kernel(a, local_only, err, stream, false);
     if (timed) cudaEventRecord(t_phase_events[1], stream);
     const long long items = seam_items(g);
-    if (!local_only && items > 0) {
+    const bool seams = !local_only && items > 0;
+    if (seams) {
         const long long blocks = (items + 255) / 256;
-        k_seams<<<(unsigned)blocks, 256, 0, stream>>>(a, items, err);
+        if ((long long)g.tiles_x * g.tiles_y <= (long long)kMergeBlocksPerSm * sm_count())
+            launch_pdl(k_seams, (unsigned)blocks, 256u, stream, a, items, err);
+        else
+            k_seams<<<(unsigned)blocks, 256, 0, stream>>>(a, items, err);
     }
     if (timed) cudaEventRecord(t_phase_events[2], stream);
-    launch_tile_kernel(a, local_only, err, stream, true);
+    launch_tile_kernel(a, local_only, err, stream, true, seams);
     if (timed) cudaEventRecord(t_phase_events[3], stream);
     if (cudaGetLastError() != cudaSuccess) return CCL_ERR_CUDA;
     return CCL_OK;

@@ -661,8 +661,11 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
     const uint32_t st = m & ~((m << 1) | mL);
     const int *tw_ = a.tws + (size_t)tile * g.tile_ints;
     const int nb = min(__ldcg(tw_), g.border_cap);
-    // final label of each border root: 1 + the key of its global root (the
-    // seam unions are complete; a read-only walk, usually one or two hops)
+    // final label of each border root: 1 + the key of its global root (a
+    // read-only walk, usually one or two hops).  Everything above reads only
+    // the local-merge output; the walk needs the seam unions complete, so a
+    // grid launched early (programmatic dependent launch) waits here.
+    pdl_wait();
     {
         const GlobalForest F{a.tws, g.tile_ints, g.off_par};
         const gnode *par = reinterpret_cast<const gnode *>(tw_ + g.off_par);
