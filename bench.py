@@ -120,6 +120,21 @@ def ncu_traffic(kernel: str):
         return None
 
 
+def ncu_warp_inst(kernel: str):
+    """Warp instructions per launch of `kernel` from the committed ncu summary,
+    if it was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_hash") != kernel_source_hash():
+            return None
+        v = d["kernels"][kernel].get("warp_inst_per_launch")
+        return float(v) if v else None
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi samples every 100 ms; keeps those inside [t0, t1]."""
 
@@ -520,6 +535,22 @@ def run_ours(args, rank, world, local):
         "path": {"bytes_per_px": PATH_BYTES_PER_PX, "achieved": round(path_gbs, 1),
                  "frac": round(path_gbs / peak, 4)},
     }
+
+    # The local merge is bound by instruction issue, not by HBM: its issue
+    # roofline is warp instructions per launch (ncu, same sources) over the
+    # launch time, against SMs x 4 schedulers x the median SM clock sampled
+    # during the timed loop.
+    winst = ncu_warp_inst("local_merge")
+    sm_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz")
+    if winst and sm_mhz and phase_ms["local_merge"] > 0:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        ach = winst / (phase_ms["local_merge"] / 1e3) / 1e12
+        pk = sms * 4 * sm_mhz * 1e6 / 1e12
+        roofline["issue"] = {"kernel": "local_merge", "bound": "issue",
+                             "achieved": round(ach, 4), "peak": round(pk, 4),
+                             "unit": "T warp-inst/s", "frac": round(ach / pk, 4),
+                             "warp_inst_per_launch": winst,
+                             "peak_source": f"{sms} SMs x 4 issue slots x {sm_mhz:.0f} MHz"}
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
