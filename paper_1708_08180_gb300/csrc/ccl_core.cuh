@@ -36,7 +36,7 @@ namespace ccl {
 constexpr int kThreads = 256;             // threads per tile = strips x words
 constexpr int kNodeCap = kThreads * 16;   // at most 16 run starts per 32-bit word
 constexpr int kBorderCapMax = 576;        // border segments: <= 2*16*NW + 2*NS for every NW
-constexpr int kHdrInts = 4;               // [0] = border-root count
+constexpr int kHdrInts = 4;               // [0] = border-root count, [1] = segment count
 
 constexpr int kQueueCap = 2048;           // unions left after the local forest pass
 constexpr int kSlotBits = 10;             // border slots per tile < 2^10
@@ -61,7 +61,8 @@ constexpr int kGlobHopBudget = 1 << 20;   // per thread per work item (global me
 
 // Geometry of one image under one tile shape, and the layout of the per-tile
 // workspace (all offsets in ints from the tile's base):
-//   [0, kHdrInts)               header: [0] = number of border roots
+//   [0, kHdrInts)               header: [0] = number of border roots, [1] = number
+//                               of segment nodes
 //   [kHdrInts, off_key)         label of each segment node (node_cap)
 //   [off_key, off_par)          smallest raster index of each border root's component
 //                               inside the tile (border_cap)

@@ -36,7 +36,7 @@ struct SmemMerge {
 
 // Shared memory of the link phase.
 struct SmemLink {
-    int S[kNodeCap];              // label per segment node
+    __align__(16) int S[kNodeCap];   // label per segment node
     int R[kBorderCapMax];         // final label per border root
     uint32_t rows[2 * kThreads];  // bit rows of the tile: [row][word]
     uint32_t st[kThreads];        // segment starts per (strip, word)
@@ -349,7 +349,10 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         const int k = sm.K[r];
         tw_[kHdrInts + n] = flagged(r) ? -(1 + k) : 1 + gkey(k);
     }
-    if (tid == 0) tw_[0] = local_only ? 0 : min(sm.nborder, g.border_cap);
+    if (tid == 0) {
+        tw_[0] = local_only ? 0 : min(sm.nborder, g.border_cap);
+        tw_[1] = total;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -648,19 +651,30 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
     const int x0 = tx * TW, y0 = ty * TH;
     const int gwi = x0 / 32 + w;
 
+    const int *tw_ = a.tws + (size_t)tile * g.tile_ints;
+    const int nb = min(__ldcg(tw_), g.border_cap);
+    const int nseg = min(__ldcg(tw_ + 1), kNodeCap);
     uint32_t rows[HS];
 #pragma unroll
     for (int j = 0; j < HS; ++j) {
         const int y = y0 + s * HS + j;
         rows[j] = (y < g.H && gwi < g.nwg) ? __ldcg(a.bits + (size_t)y * g.nwg + gwi) : 0u;
-        sm.rows[(s * HS + j) * NW + w] = rows[j];
     }
+    // the per-segment labels, copied to shared memory asynchronously
+    // (16-byte cp.async; the source starts 16 bytes into the 256-byte aligned
+    // tile workspace, and rounding the count up stays inside the workspace)
+    for (int c = tid; c < (nseg + 3) / 4; c += kThreads) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(&sm.S[4 * c]);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+                     "l"(tw_ + kHdrInts + 4 * c) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < HS; ++j) sm.rows[(s * HS + j) * NW + w] = rows[j];
     const uint32_t m = rows[0] | rows[HS - 1];
     uint32_t mL = __shfl_up_sync(0xFFFFFFFFu, m, 1);
     mL = (w > 0) ? (mL >> 31) : 0u;
     const uint32_t st = m & ~((m << 1) | mL);
-    const int *tw_ = a.tws + (size_t)tile * g.tile_ints;
-    const int nb = min(__ldcg(tw_), g.border_cap);
     // final label of each border root: 1 + the key of its global root (a
     // read-only walk, usually one or two hops).  Everything above reads only
     // the local-merge output; the walk needs the seam unions complete, so a
@@ -685,18 +699,20 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
     const int base = block_excl_scan(__popc(st), sm.warp_sums, total);   // syncs: R visible
     sm.st[tid] = st;
     sm.base[tid] = base;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();   // every thread's copies of S have landed
+    if (total != nseg) { if (tid == 0) atomicOr(err, kErrBorderCap); }
     for (int n = tid; n < total; n += kThreads) {
-        int v = __ldcg(tw_ + kHdrInts + n);
+        const int v = sm.S[n];
         if (v < 0) {
             const int j = -v - 1;
             if (j < nb) {
-                v = sm.R[j];
+                sm.S[n] = sm.R[j];
             } else {
-                v = 0;
+                sm.S[n] = 0;
                 atomicOr(err, kErrBorderCap);
             }
         }
-        sm.S[n] = v;
     }
     __syncthreads();
 
