@@ -349,6 +349,16 @@ __device__ __forceinline__ void gfind2(const GlobalForest &F, gnode &a, gnode &b
 
 __device__ __forceinline__ void gunion(const GlobalForest &F, gnode a, gnode b, int &budget,
                                        int *err) {
+    if (a == b) return;
+    {   // first try, one atomic: hook the larger node under the smaller if it is
+        // still a root (the smaller need not be one: links still only go from
+        // a larger id to a smaller); most seam pairs join sets for the first time
+        const gnode hi = a > b ? a : b, lo = a > b ? b : a;
+        const gnode old = atomicCAS(F.par(hi), hi, lo);
+        if (old == hi) return;
+        a = old;
+        b = lo;
+    }
     for (;;) {
         gfind2(F, a, b, budget, err);
         if (a == b) return;

@@ -449,9 +449,10 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
 #pragma unroll
         for (int k = 0; k < GC; ++k) d[k] = kNoNode;
         if (idx < nh_real) {
-            const long long per_row = (long long)g.nwg * kSeamGroupsPerWord;
-            const int ty = (int)(idx / per_row) + 1;
-            const int grp = (int)(idx % per_row);
+            // item counts stay below 2^32 (H * W <= 2^31 - 2): 32-bit division
+            const unsigned per_row = (unsigned)g.nwg * kSeamGroupsPerWord;
+            const int ty = (int)((unsigned)idx / per_row) + 1;
+            const int grp = (int)((unsigned)idx % per_row);
             const int j = grp / kSeamGroupsPerWord;
             const int sh = GC * (grp % kSeamGroupsPerWord);
             const int c0 = 32 * j + sh;
@@ -530,11 +531,11 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
         bool h0 = false, h1 = false, h2 = false;
         gnode kL = kNoNode, kR = kNoNode, kLu = kNoNode, kRu = kNoNode;
         if (idx < nitems) {
-            const long long v = idx - nh;
-            const int s = (int)(v % g.ns);
-            const long long t = v / g.ns;
-            const int ty = (int)(t % g.tiles_y);
-            const int tx = (int)(t / g.tiles_y) + 1;
+            const unsigned v = (unsigned)(idx - nh);
+            const int s = (int)(v % (unsigned)g.ns);
+            const unsigned t = v / (unsigned)g.ns;
+            const int ty = (int)(t % (unsigned)g.tiles_y);
+            const int tx = (int)(t / (unsigned)g.tiles_y) + 1;
             const int x = tx * g.tw;
             const int r0 = ty * g.th + s * g.hs;
             if (r0 < g.H) {
