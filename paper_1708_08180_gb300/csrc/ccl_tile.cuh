@@ -221,20 +221,19 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         atomicOr(err, kErrSmemFind);
     };
     jump();
-    // (3) hook and jump: each queued pair whose roots differ hooks the root
-    // with the larger key under the other (one CAS, no find); a hook that
-    // loses a race is queued again with the loser's new parent.  Pointer
-    // jumping then flattens the forest, and rounds repeat until no pair is
-    // left.  The final jumping leaves every node pointing at its root.
-    constexpr int kPer = kQueueCap / kThreads;   // queue entries per thread per round
-    for (int round = 0; round < 64; ++round) {
-        const int nq = min(sm.nq, kQueueCap);   // block-uniform: read after a barrier
-        if (nq == 0) break;
+    // (3) one round of hooks: each queued pair whose roots differ hooks the
+    // root with the larger key under the other (one CAS, no find); a hook
+    // that loses a race is queued again with the loser's new parent.  (4) The
+    // few pairs that lost run as lock-free unions with finds (path halving),
+    // and one more pointer jumping leaves every node pointing at its root.
+    constexpr int kPer = kQueueCap / kThreads;   // queue entries per thread
+    const int nq0 = min(sm.nq, kQueueCap);       // block-uniform: read after a barrier
+    if (nq0 > 0) {
         uint32_t e[kPer];
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const int i = tid + k * kThreads;
-            e[k] = i < nq ? sm.Q[i] : 0xFFFFFFFFu;
+            e[k] = i < nq0 ? sm.Q[i] : 0xFFFFFFFFu;
         }
         __syncthreads();
         if (tid == 0) sm.nq = 0;
@@ -253,10 +252,14 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             }
         }
         __syncthreads();
+        const int nq1 = min(sm.nq, kQueueCap);
+        for (int i = tid; i < nq1; i += kThreads) {
+            const uint32_t q = sm.Q[i];
+            sunion(sm.P, sm.K, (int)(q & 0xFFFFu), (int)(q >> 16), budget, err);
+        }
+        __syncthreads();
         jump();
     }
-    if (tid == 0 && sm.nq != 0) atomicOr(err, kErrSmemUnion);
-    __syncthreads();
 
     int *tw_ = a.tws + (size_t)tile * g.tile_ints;
     int *rec = tw_ + g.off_rec;
