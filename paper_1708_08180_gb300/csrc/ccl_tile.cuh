@@ -220,7 +220,23 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         }
         atomicOr(err, kErrSmemFind);
     };
-    jump();
+    // A first-contact tree is at most NS - 1 links deep (one per strip), so
+    // log2(NS) rounds flatten it; no test round is needed here because the
+    // hooks below tolerate a parent that is not a root (the CAS fails and
+    // the pair is unioned with finds), and the final jumping tests.
+    {
+        constexpr int kRounds = NS >= 256 ? 8 : NS >= 128 ? 7 : NS >= 64 ? 6 : 5;
+#pragma unroll 1
+        for (int round = 0; round < kRounds; ++round) {
+#pragma unroll 4
+            for (int n = tid; n < total; n += kThreads) {
+                const int p = sm.P[n];
+                const int gp = sm.P[p];
+                if (gp != p) sm.P[n] = (pnode)gp;
+            }
+            __syncthreads();
+        }
+    }
     // (3) one round of hooks: each queued pair whose roots differ hooks the
     // root with the larger key under the other (one CAS, no find); a hook
     // that loses a race is queued again with the loser's new parent.  (4) The
@@ -258,8 +274,8 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             sunion(sm.P, sm.K, (int)(q & 0xFFFFu), (int)(q >> 16), budget, err);
         }
         __syncthreads();
-        jump();
     }
+    jump();
 
     int *tw_ = a.tws + (size_t)tile * g.tile_ints;
     int *rec = tw_ + g.off_rec;
