@@ -148,8 +148,10 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     // root is its smallest key.  A contact whose CAS fails is the union of its
     // upper segment with the parent already taken; it is queued.  (2) Pointer
     // jumping, in lock-step rounds, flattens the forest.  (3) The queued
-    // unions are shared out evenly over the block (CAS link of the larger-key
-    // root under the smaller).  (4) Every node is pointed straight at its root.
+    // unions are shared out evenly over the block: one CAS hook each of the
+    // larger-key root under the smaller; (4) the few that lose a race run as
+    // lock-free unions with finds.  (5) Pointer jumping points every node
+    // straight at its root.
     int budget = kSmemHopBudget;
     if (s > 0) {
         const int up = tid - NW;
@@ -203,23 +205,10 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         }
     }
     __syncthreads();
-    // (2) pointer jumping until every node points at its tree's root
+    // (2) pointer jumping: every node to the root of its first-contact tree
     volatile pnode *vP = sm.P;
     // Plain loads: within a round any mix of old and new parents is valid
     // (all are ancestors), and the barrier between rounds publishes the stores.
-    auto jump = [&]() {
-        for (int round = 0; round < 64; ++round) {
-            int changed = 0;
-#pragma unroll 4
-            for (int n = tid; n < total; n += kThreads) {
-                const int p = sm.P[n];
-                const int gp = sm.P[p];
-                if (gp != p) { sm.P[n] = (pnode)gp; changed = 1; }
-            }
-            if (!__syncthreads_or(changed)) return;
-        }
-        atomicOr(err, kErrSmemFind);
-    };
     // A first-contact tree is at most NS - 1 links deep (one per strip), so
     // log2(NS) rounds flatten it; no test round is needed here because the
     // hooks below tolerate a parent that is not a root (the CAS fails and
@@ -240,14 +229,15 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     // (3) one round of hooks: each queued pair whose roots differ hooks the
     // root with the larger key under the other (one CAS, no find); a hook
     // that loses a race is queued again with the loser's new parent.  (4) The
-    // few pairs that lost run as lock-free unions with finds (path halving),
-    // and one more pointer jumping leaves every node pointing at its root.
+    // few pairs that lost run as lock-free unions with finds (path halving).
     constexpr int kPer = kQueueCap / kThreads;   // queue entries per thread
     const int nq0 = min(sm.nq, kQueueCap);       // block-uniform: read after a barrier
     if (nq0 > 0) {
+        const int kn = (nq0 + kThreads - 1) / kThreads;   // entries per thread (block-uniform)
         uint32_t e[kPer];
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
+            if (k >= kn) break;
             const int i = tid + k * kThreads;
             e[k] = i < nq0 ? sm.Q[i] : 0xFFFFFFFFu;
         }
@@ -256,6 +246,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
+            if (k >= kn) break;
             if (e[k] == 0xFFFFFFFFu) continue;
             int pa = vP[e[k] & 0xFFFFu], pb = vP[e[k] >> 16];
             if (pa == pb) continue;
@@ -275,7 +266,18 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         }
         __syncthreads();
     }
-    jump();
+    // (5) pointer jumping until every node points at its root
+    for (int round = 0; round < 64; ++round) {
+        int changed = 0;
+#pragma unroll 4
+        for (int n = tid; n < total; n += kThreads) {
+            const int p = sm.P[n];
+            const int gp = sm.P[p];
+            if (gp != p) { sm.P[n] = (pnode)gp; changed = 1; }
+        }
+        if (!__syncthreads_or(changed)) break;
+        if (round == 63) atomicOr(err, kErrSmemFind);
+    }
 
     int *tw_ = a.tws + (size_t)tile * g.tile_ints;
     int *rec = tw_ + g.off_rec;
