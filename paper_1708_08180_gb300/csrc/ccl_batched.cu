@@ -60,7 +60,7 @@ __device__ __forceinline__ int find_image_by_chunk(const BatchImage *imgs, int n
 }
 
 template <int HS>
-__global__ void __launch_bounds__(kThreads) kb_merge(BatchHeader *hdr, const BatchImage *imgs,
+__global__ void __launch_bounds__(kThreads, 6) kb_merge(BatchHeader *hdr, const BatchImage *imgs,
                                                      int *err) {
     __shared__ SmemMerge sm;
     __shared__ int s_tile, s_img;
@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(256, 4) kb_seams(BatchHeader *hdr, const Batch
     __shared__ int s_img;
     const int n = hdr->n;
     const long long total = hdr->total_chunks;
+    pdl_launch_dependents();   // the link kernel may start (it waits before its walks)
     for (;;) {
         if (threadIdx.x == 0) {
             const long long c = atomicAdd(&hdr->seam_ctr, 1);
@@ -238,11 +239,11 @@ void launch_kernels(const Persist &p, int conn, BatchHeader *hdr, const BatchIma
     if (conn == 8) {
         kb_merge<2><<<p.merge_blocks, kThreads, 0, s>>>(hdr, imgs, err);
         kb_seams<<<p.seam_blocks, 256, 0, s>>>(hdr, imgs, err);
-        kb_link<2><<<p.link_blocks, kThreads, 0, s>>>(hdr, imgs, err);
+        launch_pdl(kb_link<2>, (unsigned)p.link_blocks, (unsigned)kThreads, s, hdr, imgs, err);
     } else {
         kb_merge<1><<<p.merge_blocks, kThreads, 0, s>>>(hdr, imgs, err);
         kb_seams<<<p.seam_blocks, 256, 0, s>>>(hdr, imgs, err);
-        kb_link<1><<<p.link_blocks, kThreads, 0, s>>>(hdr, imgs, err);
+        launch_pdl(kb_link<1>, (unsigned)p.link_blocks, (unsigned)kThreads, s, hdr, imgs, err);
     }
 }
 

@@ -6,6 +6,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <utility>
 
 #include "../../include/ccl.h"
 
@@ -30,6 +31,26 @@ constexpr int kTileClasses = 7;   // extents <= 64, 128, 256, 512, 1024, 2048, >
 int tile_class(int extent);
 int default_tile_width(int height, int width, int conn);
 void set_tile_table_entry(int conn, int hc, int wc, int tile_w);
+
+// Launch with programmatic stream serialisation: the grid may start once
+// every block of the previous grid on the stream has called
+// griddepcontrol.launch_dependents (or exited); it must griddepcontrol.wait
+// before reading that grid's results.
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), unsigned grid, unsigned block, cudaStream_t s,
+                              A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 // Release batched-path state.
 void free_batched_state();

@@ -56,23 +56,6 @@ static int sm_count() {
     return n;
 }
 
-// launch with programmatic stream serialisation (see k_merge)
-template <typename... P, typename... A>
-static cudaError_t launch_pdl(void (*kernel)(P...), unsigned grid, unsigned block, cudaStream_t s,
-                              A &&...args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
-}
-
 // link_early: the link kernel directly follows the seam kernel and may start
 // early; otherwise (no seam kernel ran) it waits for the local merge as usual
 template <int NW, int HS>

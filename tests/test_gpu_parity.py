@@ -197,3 +197,25 @@ def test_library_workspace_when_none_given():
     assert st == 0
     ccl.ccl_sync()
     assert_same(out.cpu().numpy(), oracle.label(img, 8), "library workspace")
+
+
+@pytest.mark.parametrize("n", [1024, 4096])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_back_to_back_calls_share_workspace(n, conn):
+    """Calls queued without a host sync in between, all on one workspace:
+    each call's kernels start early where the launch allows it (programmatic
+    dependent launch of the seam and link kernels), so the next call must not
+    touch the workspace before the previous link kernel is done with it.
+    1024^2 is a one-wave local merge (seam kernel launched early as well)."""
+    imgs = [synthetic.bernoulli(n, n, p, 40 + k, cfg_id=27) for k, p in enumerate((0.45, 0.6, 0.3, 0.5))]
+    wants = [oracle.label(im, conn) for im in imgs]
+    ws = torch.empty(ccl.ccl_workspace_bytes(n, n, conn), dtype=torch.uint8, device=DEV)
+    dimgs = [torch.from_numpy(im).to(DEV) for im in imgs]
+    outs = [torch.full((n, n), -7, dtype=torch.int32, device=DEV) for _ in imgs]
+    torch.cuda.synchronize()
+    for _ in range(3):
+        for d, o in zip(dimgs, outs):
+            ccl.ccl_label(d, conn, out=o, ws=ws)
+    ccl.ccl_sync()
+    for k, (o, want) in enumerate(zip(outs, wants)):
+        assert_same(o.cpu().numpy(), want, f"back-to-back call {k}")
