@@ -138,6 +138,19 @@ def test_repeat_runs_identical(conn):
         assert_same(out.cpu().numpy(), want, "repeat")
 
 
+@pytest.mark.parametrize("n", [1024, 2048])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_density_sweep_full_range(n, conn):
+    """Densities 0.1 ... 0.9 in steps of 0.1, two seeds each, at 1024^2 and
+    2048^2 (the sweep of the plain-path workload at sizes the oracle labels
+    in a fraction of a second)."""
+    for k in range(1, 10):
+        p = k / 10
+        for seed in (0, 1):
+            img = synthetic.bernoulli(n, n, p, seed)
+            assert_same(gpu_label(img, conn), oracle.label(img, conn), f"{n} p={p} seed={seed}")
+
+
 @pytest.mark.parametrize("p", [0.1, 0.4, 0.5, 0.6, 0.9])
 @pytest.mark.parametrize("conn", [4, 8])
 def test_density_sweep_4096(p, conn):
