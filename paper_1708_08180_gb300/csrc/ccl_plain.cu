@@ -9,34 +9,6 @@
 
 namespace ccl {
 
-// The link kernel is launched with programmatic stream serialisation: once
-// every seam block has started (and passed its own wait), link blocks may
-// start and run the part of their prologue that reads only the local-merge
-// output, then wait (pdl_wait in link_tile) for the seam unions.  When the
-// local merge fits in one wave of blocks the seam kernel is launched the
-// same way, so that its launch overlaps the local merge's last blocks; its
-// blocks wait for the local merge before reading anything.
-template <int NW, int HS>
-__global__ void __launch_bounds__(kThreads) k_merge(ImageArgs a, int local_only, int *err) {
-    __shared__ SmemMerge sm;
-    pdl_launch_dependents();
-    merge_tile<NW, HS>(a, blockIdx.x, local_only != 0, sm, err);
-}
-
-__global__ void __launch_bounds__(256, 4) k_seams(ImageArgs a, long long nitems, int *err) {
-    __shared__ SmemSeams sm;
-    pdl_wait();
-    pdl_launch_dependents();
-    seam_block(a, (long long)blockIdx.x * 256, nitems, sm, err);
-}
-
-
-template <int NW, int HS>
-__global__ void __launch_bounds__(kThreads, 8) k_link(ImageArgs a, int *err) {
-    __shared__ SmemLink sm;
-    link_tile<NW, HS>(a, blockIdx.x, sm, err);
-}
-
 // local-merge blocks resident per SM (shared memory: 6 x SmemMerge)
 constexpr int kMergeBlocksPerSm = 6;
 
@@ -56,13 +28,48 @@ static int sm_count() {
     return n;
 }
 
+// The link kernel is launched with programmatic stream serialisation: once
+// every seam block has started (and passed its own wait), link blocks may
+// start and run the part of their prologue that reads only the local-merge
+// output, then wait (pdl_wait in link_tile) for the seam unions.  When the
+// local merge fits in one wave of blocks the seam kernel is launched the
+// same way, so that its launch overlaps the local merge's last blocks; its
+// blocks wait for the local merge before reading anything.  When it takes
+// several waves the local merge itself is launched that way, so that its
+// blocks are resident when the previous grid on the stream ends; they wait
+// for that grid (pdl_wait) before reading anything.
+template <int NW, int HS>
+__global__ void __launch_bounds__(kThreads) k_merge(ImageArgs a, int local_only, int *err) {
+    __shared__ SmemMerge sm;
+    pdl_wait();
+    pdl_launch_dependents();
+    merge_tile<NW, HS>(a, blockIdx.x, local_only != 0, sm, err);
+}
+
+__global__ void __launch_bounds__(256, 4) k_seams(ImageArgs a, long long nitems, int *err) {
+    __shared__ SmemSeams sm;
+    pdl_wait();
+    pdl_launch_dependents();
+    seam_block(a, (long long)blockIdx.x * 256, nitems, sm, err);
+}
+
+
+template <int NW, int HS>
+__global__ void __launch_bounds__(kThreads, 8) k_link(ImageArgs a, int *err) {
+    __shared__ SmemLink sm;
+    pdl_launch_dependents();
+    link_tile<NW, HS>(a, blockIdx.x, sm, err);
+}
+
 // link_early: the link kernel directly follows the seam kernel and may start
 // early; otherwise (no seam kernel ran) it waits for the local merge as usual
 template <int NW, int HS>
 static void launch_merge_link(const ImageArgs &a, bool local_only, int *err, cudaStream_t s,
                               bool link, bool link_early) {
     const int ntiles = a.g.tiles_x * a.g.tiles_y;
-    if (!link)
+    if (!link && ntiles > kMergeBlocksPerSm * sm_count())
+        launch_pdl(k_merge<NW, HS>, (unsigned)ntiles, (unsigned)kThreads, s, a, local_only ? 1 : 0, err);
+    else if (!link)
         k_merge<NW, HS><<<ntiles, kThreads, 0, s>>>(a, local_only ? 1 : 0, err);
     else if (link_early)
         launch_pdl(k_link<NW, HS>, (unsigned)ntiles, (unsigned)kThreads, s, a, err);
