@@ -137,6 +137,32 @@ __device__ __forceinline__ void pdl_launch_dependents() {
 }
 
 // ---------------------------------------------------------------------------
+// L2 eviction priorities: what the local merge writes for the seam and link
+// kernels (bit image, per-tile records, labels, parents; ~60 MB at 8192^2)
+// is stored with evict-last priority, so that it outlives the streamed input
+// image and label writes in L2 until those kernels read it.
+__device__ __forceinline__ unsigned long long l2_evict_last() {
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void st_policy(uint32_t *p, uint32_t v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_policy(int *p, int v, unsigned long long pol) {
+    st_policy(reinterpret_cast<uint32_t *>(p), (uint32_t)v, pol);
+}
+__device__ __forceinline__ void st_policy(unsigned long long *p, unsigned long long v,
+                                          unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_policy(long long *p, long long v, unsigned long long pol) {
+    st_policy(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v, pol);
+}
+
+// ---------------------------------------------------------------------------
 // bit helpers
 
 // mask of bits 0..x (x in [-1, 31]); x = -1 gives 0

@@ -85,7 +85,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
                       ? load_row_bits(a.img, img_end, y, gx, g.W, a.aligned16 != 0)
                       : 0u;
         if (y < g.H && (x0 / 32 + w) < g.nwg)
-            a.bits[(size_t)y * g.nwg + (x0 / 32 + w)] = rows[j];
+            st_policy(a.bits + (size_t)y * g.nwg + (x0 / 32 + w), rows[j], l2_evict_last());
     }
     const uint32_t top = rows[0], bot = rows[HS - 1];
     const uint32_t m = top | bot;
@@ -338,8 +338,8 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
                 const int j = atomicAdd(&sm.nborder, 1);
                 if (j < g.border_cap) {
                     const int gk = gkey(sm.K[n]);
-                    tw_[g.off_key + j] = gk;
-                    par[j] = make_gnode(gk, tile, j);
+                    st_policy(tw_ + g.off_key + j, gk, l2_evict_last());
+                    st_policy(par + j, make_gnode(gk, tile, j), l2_evict_last());
                     sm.K[n] = (uint16_t)j;
                 } else {
                     atomicOr(err, kErrBorderCap);
@@ -356,19 +356,19 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
                                       : (long long)kNoNode;
     };
     if (tid < TW) {
-        rec64[tid] = node_of(r_top);
-        rec64[TW + tid] = node_of(r_bot);
+        st_policy(rec64 + tid, node_of(r_top), l2_evict_last());
+        st_policy(rec64 + TW + tid, node_of(r_bot), l2_evict_last());
     }
     if (tid < NS) {
-        rec64[2 * TW + tid] = node_of(r_left);
-        rec64[2 * TW + NS + tid] = node_of(r_right);
+        st_policy(rec64 + 2 * TW + tid, node_of(r_left), l2_evict_last());
+        st_policy(rec64 + 2 * TW + NS + tid, node_of(r_right), l2_evict_last());
     }
 
     // ---- per-segment labels ----
     for (int n = tid; n < total; n += kThreads) {
         const int r = sm.P[n];
         const int k = sm.K[r];
-        tw_[kHdrInts + n] = flagged(r) ? -(1 + k) : 1 + gkey(k);
+        st_policy(tw_ + kHdrInts + n, flagged(r) ? -(1 + k) : 1 + gkey(k), l2_evict_last());
     }
     if (tid == 0) {
         tw_[0] = local_only ? 0 : min(sm.nborder, g.border_cap);
