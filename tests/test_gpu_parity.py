@@ -232,3 +232,20 @@ def test_back_to_back_calls_share_workspace(n, conn):
     ccl.ccl_sync()
     for k, (o, want) in enumerate(zip(outs, wants)):
         assert_same(o.cpu().numpy(), want, f"back-to-back call {k}")
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_workspace_bound_is_respected(conn):
+    """A workspace of exactly ccl_workspace_bytes_tiled bytes, followed by a
+    guard region: no call writes past the size it asked for."""
+    img = synthetic.bernoulli(777, 1500, 0.5, 3, cfg_id=28)
+    want = oracle.label(img, conn)
+    dimg = torch.from_numpy(img).to(DEV)
+    for tw in TILES:
+        need = ccl.ccl_workspace_bytes_tiled(777, 1500, conn, tw)
+        buf = torch.full((need + 4096,), 0xAB, dtype=torch.uint8, device=DEV)
+        out = torch.empty((777, 1500), dtype=torch.int32, device=DEV)
+        ccl.ccl_label_tiled(dimg, conn, tw, out=out, ws=buf[:need])
+        ccl.ccl_sync()
+        assert_same(out.cpu().numpy(), want, f"tile {tw}")
+        assert bool((buf[need:] == 0xAB).all()), f"tile {tw}: write past the workspace"
