@@ -438,6 +438,35 @@ def served_vs_plain(device_index: int, rates=(2000.0, 10000.0), seconds: float =
     return out
 
 
+def stats_leg(labels, stream, reps: int = 50):
+    """ccl_component_stats on the headline image's labels (count, bounding box
+    and coordinate sums of every component, in label order): device time per
+    call (CUDA events, after warm-up) and the number of components."""
+    import torch
+
+    import paper_1708_08180_gb300 as ccl
+
+    h, w = labels.shape
+    ws = torch.empty(ccl.ccl_stats_workspace_bytes(h, w), dtype=torch.uint8, device=labels.device)
+    _, ncomps = ccl.ccl_component_stats(labels, 0, ws=ws, stream=stream)
+    torch.cuda.synchronize()
+    n = int(ncomps.item())
+    comps = torch.empty((max(n, 1), ccl.COMPONENT_WORDS), dtype=torch.int32, device=labels.device)
+    for _ in range(3):
+        ccl.ccl_component_stats(labels, n, comps=comps, ncomps=ncomps, ws=ws, stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ccl.ccl_component_stats(labels, n, comps=comps, ncomps=ncomps, ws=ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ccl.ccl_sync(stream)
+    ms = e0.elapsed_time(e1) / reps
+    return {"components": n, "ms": round(ms, 5), "gpix_s": round(h * w / (ms / 1e3) / 1e9, 2),
+            "what": "pixel count, bounding box and coordinate sums of every component"}
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -573,6 +602,8 @@ def run_ours(args, rank, world, local):
     }
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e_server(host_imgs[0], K, local)
+    if rank == 0 and not args.no_stats:
+        line["component_stats"] = stats_leg(outs[0], stream)
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_vs_plain(local)
     if rank == 0 and not args.no_served:
@@ -596,6 +627,7 @@ def main(argv=None) -> int:
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stats", action="store_true", help="skip the component-statistics leg")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-vs-plain leg (256 images of 64..2048)")
     ap.add_argument("--no-served", action="store_true",

@@ -108,9 +108,8 @@ size_t ccl_workspace_bytes_tiled(int height, int width, int connectivity, int ti
 /* Label one image (all three phases: local merge §II-A, boundary analysis
  * §II-B, link §II-C) with the default tile width.
  *   d_img    : device, height*width bytes, nonzero = foreground (read only)
- *   d_labels : device, height*width int32, fully overwritten (the link phase
- *              also uses it as the global union-find array, so it must not
- *              alias d_img or the workspace)
+ *   d_labels : device, height*width int32, fully overwritten by the link
+ *              phase (it must not alias d_img or the workspace)
  *   d_ws     : device workspace of ws_bytes >= ccl_workspace_bytes(), or NULL
  *   stream   : CUDA stream to enqueue on
  * Returns CCL_OK once the three kernels are enqueued. */
@@ -181,6 +180,44 @@ ccl_status ccl_shutdown(void);
 #define CCL_STATIC_SCRATCH_BYTES (64u << 20)
 ccl_status ccl_label_static(const uint8_t *d_img, int32_t *d_labels, int height, int width,
                             int connectivity, ccl_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Component statistics                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Statistics of one component of a canonical label image: the size and
+ * location of each region, which the paper's motivating uses need (§I). */
+typedef struct {
+    int32_t label;        /* 1 + smallest raster index of the component */
+    int32_t count;        /* pixels */
+    int32_t xmin, ymin;   /* bounding box, inclusive */
+    int32_t xmax, ymax;
+    int64_t sum_x;        /* sums of the pixels' coordinates: the centroid is */
+    int64_t sum_y;        /* (sum_x / count, sum_y / count)                    */
+} ccl_component;
+
+/* Bytes of workspace ccl_component_stats needs for a height x width label
+ * image (per-row root counts and the sorted list of component roots, sized for
+ * the most components an image can hold).  0 on invalid arguments. */
+size_t ccl_stats_workspace_bytes(int height, int width);
+
+/* Statistics of every component of d_labels, a canonical label image as
+ * ccl_label writes it (device, height*width int32, read only; any other
+ * content gives unspecified statistics but stays in bounds).
+ *   d_comps   : device array of max_comps records (max_comps >= 0), written
+ *               in increasing label order; components beyond max_comps are
+ *               counted but not written
+ *   d_ncomps  : device int32, receives the number of components
+ *   d_ws      : device workspace of ws_bytes >= ccl_stats_workspace_bytes(),
+ *               or NULL (library-owned, as for ccl_label)
+ * A component's root is its one pixel whose label is 1 + its own index; the
+ * roots are counted per row segment, ranked by a prefix sum, and every tile
+ * of 256 x 64 pixels adds its pixels' contributions into the records of their
+ * components (shared-memory aggregation, then one atomic update per
+ * component and tile).  Enqueues four kernels on `stream`. */
+ccl_status ccl_component_stats(const int32_t *d_labels, int height, int width,
+                               ccl_component *d_comps, int max_comps, int32_t *d_ncomps,
+                               void *d_ws, size_t ws_bytes, ccl_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Batched: many images of different sizes in one launch sequence           */

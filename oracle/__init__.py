@@ -22,6 +22,9 @@ Functions
   * ``seam_pairs(h, w, conn, tile_w, tile_h)`` -- the cross-tile adjacent pixel
     pairs the boundary analysis must union (§II-B, Eq. 1-2), enumerated one by
     one.
+  * ``component_stats(labels)`` -- per component of a canonical label image:
+    pixel count, inclusive bounding box and coordinate sums (the size and
+    location of each region, §I), by definition, in label order.
 """
 from __future__ import annotations
 
@@ -180,3 +183,35 @@ def seam_pairs(h: int, w: int, conn: int, tile_w: int, tile_h: int):
                 p, q = y * w + x, qy * w + qx
                 pairs.add((min(p, q), max(p, q)))
     return pairs
+
+
+def component_stats(labels: np.ndarray) -> dict:
+    """Statistics of every component of a canonical label image, in increasing
+    label order: ``label``, ``count`` (pixels), ``xmin ymin xmax ymax``
+    (inclusive bounding box), ``sum_x sum_y`` (sums of the pixels' coordinates;
+    the centroid is sum / count).  Plain definition: group the foreground
+    pixels by label and reduce each group."""
+    lab = np.asarray(labels)
+    h, w = lab.shape
+    ys, xs = np.nonzero(lab)
+    vals = lab[ys, xs].astype(np.int64)
+    if vals.size == 0:
+        z = np.zeros(0, dtype=np.int64)
+        return {k: z for k in ("label", "count", "xmin", "ymin", "xmax", "ymax", "sum_x", "sum_y")}
+    uniq, inv = np.unique(vals, return_inverse=True)
+    n = uniq.size
+    count = np.bincount(inv, minlength=n).astype(np.int64)
+    xmin = np.full(n, np.iinfo(np.int64).max, dtype=np.int64)
+    ymin = xmin.copy()
+    xmax = np.full(n, -1, dtype=np.int64)
+    ymax = xmax.copy()
+    np.minimum.at(xmin, inv, xs)
+    np.minimum.at(ymin, inv, ys)
+    np.maximum.at(xmax, inv, xs)
+    np.maximum.at(ymax, inv, ys)
+    sum_x = np.bincount(inv, weights=xs.astype(np.float64), minlength=n)
+    sum_y = np.bincount(inv, weights=ys.astype(np.float64), minlength=n)
+    return {"label": uniq, "count": count, "xmin": xmin, "ymin": ymin, "xmax": xmax,
+            "ymax": ymax, "sum_x": np.rint(sum_x).astype(np.int64),
+            "sum_y": np.rint(sum_y).astype(np.int64)}
+

@@ -25,7 +25,13 @@ __all__ = [
     "ccl_batched_workspace_bytes", "ccl_default_tile_width", "ccl_seam_pair_count", "ccl_sync",
     "ccl_shutdown", "ccl_status_string", "ccl_set_phase_events", "ccl_label_static", "Server",
     "ccl_get_tile_table", "ccl_set_tile_table", "ccl_autotune", "load",
+    "ccl_stats_workspace_bytes", "ccl_component_stats", "component_stats", "COMPONENT_FIELDS",
 ]
+
+# ccl_component as int32 words: label, count, xmin, ymin, xmax, ymax, then the
+# int64 sums of x and y (two words each)
+COMPONENT_WORDS = 10
+COMPONENT_FIELDS = ("label", "count", "xmin", "ymin", "xmax", "ymax", "sum_x", "sum_y")
 
 
 def _torch():
@@ -226,6 +232,53 @@ def ccl_autotune(conn: int = 8, reps: int = 3, stream=None) -> List[List[int]]:
 
 def ccl_shutdown() -> None:
     check(load().ccl_shutdown(), "ccl_shutdown")
+
+
+def ccl_stats_workspace_bytes(height: int, width: int) -> int:
+    return int(load().ccl_stats_workspace_bytes(height, width))
+
+
+def ccl_component_stats(labels, max_comps: int, comps=None, ncomps=None, ws=None, stream=None):
+    """Enqueue the statistics of every component of a canonical CUDA int32
+    label image.  ``comps``: CUDA int32 tensor (max_comps, 10) receiving the
+    records (COMPONENT_FIELDS, the sums as int64 word pairs), in label order;
+    ``ncomps``: CUDA int32 tensor (1,) receiving the component count.  Both
+    are allocated here when None.  Returns (comps, ncomps)."""
+    torch = _torch()
+    if not isinstance(labels, torch.Tensor) or not labels.is_cuda or labels.dtype != torch.int32 \
+            or labels.dim() != 2 or not labels.is_contiguous():
+        raise TypeError("labels must be a contiguous 2-D int32 CUDA tensor")
+    h, w = labels.shape
+    if comps is None:
+        comps = torch.empty((max(max_comps, 1), COMPONENT_WORDS), dtype=torch.int32,
+                            device=labels.device)
+    if ncomps is None:
+        ncomps = torch.empty(1, dtype=torch.int32, device=labels.device)
+    if ws is None:
+        ws = _workspace(ccl_stats_workspace_bytes(h, w), labels.device)
+    check(load().ccl_component_stats(labels.data_ptr(), h, w, comps.data_ptr(), max_comps,
+                                     ncomps.data_ptr(), ws.data_ptr(), ws.numel(),
+                                     _stream_handle(stream)), "ccl_component_stats")
+    return comps, ncomps
+
+
+def component_stats(labels) -> dict:
+    """Statistics of every component of a canonical CUDA label image (blocking):
+    a dict of CPU numpy arrays keyed by COMPONENT_FIELDS, in label order."""
+    import numpy as np
+
+    h, w = labels.shape
+    ws = _workspace(ccl_stats_workspace_bytes(h, w), labels.device)
+    _, ncomps = ccl_component_stats(labels, 0, ws=ws)         # the count first
+    n = int(ncomps.item())
+    comps, ncomps = ccl_component_stats(labels, n, ws=ws)     # then the records
+    ccl_sync()
+    raw = comps[:n].cpu().numpy()
+    out = {f: raw[:, k].astype(np.int64) for k, f in enumerate(COMPONENT_FIELDS[:6])}
+    wide = raw[:, 6:10].copy().view(np.int64)
+    out["sum_x"] = wide[:, 0]
+    out["sum_y"] = wide[:, 1]
+    return out
 
 
 def label(img, conn: int = 8, tile_w: int = 0):

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libccl.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_SOURCES = ["ccl_runtime.cu", "ccl_plain.cu", "ccl_batched.cu", "ccl_noalloc.cu",
+CUDA_SOURCES = ["ccl_runtime.cu", "ccl_plain.cu", "ccl_batched.cu", "ccl_noalloc.cu", "ccl_stats.cu",
                 "ccl_autotune.cu"]
 CXX_SOURCES = ["ccl_server.cpp"]
 

@@ -195,3 +195,54 @@ def test_seam_pair_closed_form(hw, tile, conn):
         # Eq. 1-2 (with N = width, M = height), minus the image-edge seam they
         # include: P_x = (W/b_x - 1) * H, P_y = (H/b_y - 1) * W
         assert len(pairs) == (w // tw - 1) * h + (h // th - 1) * w
+
+
+# ---- component statistics (size and location of each region, §I) ----
+
+def test_component_stats_hand_example():
+    # 4-connectivity: {(0,0),(0,1)} -> 1, {(0,2)} -> 3, {(2,1),(2,2)} -> 8 (x, y)
+    lab = oracle.label(np.array([[1, 0, 1], [1, 0, 0], [0, 1, 1]], dtype=np.uint8), 4)
+    st = oracle.component_stats(lab)
+    assert st["label"].tolist() == [1, 3, 8]
+    assert st["count"].tolist() == [2, 1, 2]
+    assert st["xmin"].tolist() == [0, 2, 1] and st["xmax"].tolist() == [0, 2, 2]
+    assert st["ymin"].tolist() == [0, 0, 2] and st["ymax"].tolist() == [1, 0, 2]
+    assert st["sum_x"].tolist() == [0, 2, 3] and st["sum_y"].tolist() == [1, 0, 4]
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_component_stats_against_pixel_loop(conn):
+    """Against a pixel-by-pixel Python loop on small seeded images."""
+    for seed in range(6):
+        img = synthetic.bernoulli(13 + seed, 17 + 2 * seed, 0.45, seed, cfg_id=60)
+        lab = oracle.label(img, conn)
+        acc = {}
+        h, w = lab.shape
+        for y in range(h):
+            for x in range(w):
+                L = int(lab[y, x])
+                if L:
+                    c = acc.setdefault(L, [0, x, y, x, y, 0, 0])
+                    c[0] += 1
+                    c[1] = min(c[1], x); c[2] = min(c[2], y)
+                    c[3] = max(c[3], x); c[4] = max(c[4], y)
+                    c[5] += x; c[6] += y
+        st = oracle.component_stats(lab)
+        assert st["label"].tolist() == sorted(acc)
+        for k, L in enumerate(sorted(acc)):
+            c = acc[L]
+            got = [st[f][k] for f in ("count", "xmin", "ymin", "xmax", "ymax", "sum_x", "sum_y")]
+            assert got == c, (L, got, c)
+            # the root pixel (label - 1) is the component's first pixel in raster order
+            assert (L - 1) // w == c[2]
+
+
+def test_component_stats_closed_forms():
+    h, w = 12, 20
+    full = oracle.component_stats(oracle.label(synthetic.full(h, w), 8))
+    assert full["label"].tolist() == [1] and full["count"].tolist() == [h * w]
+    assert full["sum_x"].tolist() == [h * w * (w - 1) // 2]
+    assert full["sum_y"].tolist() == [w * h * (h - 1) // 2]
+    assert oracle.component_stats(oracle.label(synthetic.empty(h, w), 4))["count"].size == 0
+    cb = oracle.component_stats(oracle.label(synthetic.checkerboard(h, w), 4))
+    assert cb["count"].size == h * w // 2 and set(cb["count"].tolist()) == {1}
