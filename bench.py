@@ -447,10 +447,11 @@ def stats_leg(labels, stream, reps: int = 50):
     import paper_1708_08180_gb300 as ccl
 
     h, w = labels.shape
-    ws = torch.empty(ccl.ccl_stats_workspace_bytes(h, w), dtype=torch.uint8, device=labels.device)
-    _, ncomps = ccl.ccl_component_stats(labels, 0, ws=ws, stream=stream)
+    _, ncomps = ccl.ccl_component_stats(labels, 0, stream=stream)
     torch.cuda.synchronize()
     n = int(ncomps.item())
+    ws = torch.empty(ccl.ccl_stats_workspace_bytes(h, w, n), dtype=torch.uint8,
+                     device=labels.device)
     comps = torch.empty((max(n, 1), ccl.COMPONENT_WORDS), dtype=torch.int32, device=labels.device)
     for _ in range(3):
         ccl.ccl_component_stats(labels, n, comps=comps, ncomps=ncomps, ws=ws, stream=stream)

@@ -197,9 +197,10 @@ typedef struct {
 } ccl_component;
 
 /* Bytes of workspace ccl_component_stats needs for a height x width label
- * image (per-row root counts and the sorted list of component roots, sized for
- * the most components an image can hold).  0 on invalid arguments. */
-size_t ccl_stats_workspace_bytes(int height, int width);
+ * image and max_comps records: root counts per row segment, the sorted list
+ * of component roots (sized for the most components an image can hold) and
+ * per-field accumulators for max_comps components.  0 on invalid arguments. */
+size_t ccl_stats_workspace_bytes(int height, int width, int max_comps);
 
 /* Statistics of every component of d_labels, a canonical label image as
  * ccl_label writes it (device, height*width int32, read only; any other
@@ -212,9 +213,10 @@ size_t ccl_stats_workspace_bytes(int height, int width);
  *               or NULL (library-owned, as for ccl_label)
  * A component's root is its one pixel whose label is 1 + its own index; the
  * roots are counted per row segment, ranked by a prefix sum, and every tile
- * of 256 x 64 pixels adds its pixels' contributions into the records of their
- * components (shared-memory aggregation, then one atomic update per
- * component and tile).  Enqueues four kernels on `stream`. */
+ * of 256 x 64 pixels adds its pixels' contributions into the accumulators of
+ * their components (shared-memory aggregation, then one atomic update per
+ * field, component and tile), packed into the records at the end.  Enqueues
+ * seven kernels on `stream`. */
 ccl_status ccl_component_stats(const int32_t *d_labels, int height, int width,
                                ccl_component *d_comps, int max_comps, int32_t *d_ncomps,
                                void *d_ws, size_t ws_bytes, ccl_stream stream);

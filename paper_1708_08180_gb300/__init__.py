@@ -234,8 +234,8 @@ def ccl_shutdown() -> None:
     check(load().ccl_shutdown(), "ccl_shutdown")
 
 
-def ccl_stats_workspace_bytes(height: int, width: int) -> int:
-    return int(load().ccl_stats_workspace_bytes(height, width))
+def ccl_stats_workspace_bytes(height: int, width: int, max_comps: int) -> int:
+    return int(load().ccl_stats_workspace_bytes(height, width, max_comps))
 
 
 def ccl_component_stats(labels, max_comps: int, comps=None, ncomps=None, ws=None, stream=None):
@@ -255,7 +255,7 @@ def ccl_component_stats(labels, max_comps: int, comps=None, ncomps=None, ws=None
     if ncomps is None:
         ncomps = torch.empty(1, dtype=torch.int32, device=labels.device)
     if ws is None:
-        ws = _workspace(ccl_stats_workspace_bytes(h, w), labels.device)
+        ws = _workspace(ccl_stats_workspace_bytes(h, w, max_comps), labels.device)
     check(load().ccl_component_stats(labels.data_ptr(), h, w, comps.data_ptr(), max_comps,
                                      ncomps.data_ptr(), ws.data_ptr(), ws.numel(),
                                      _stream_handle(stream)), "ccl_component_stats")
@@ -267,11 +267,9 @@ def component_stats(labels) -> dict:
     a dict of CPU numpy arrays keyed by COMPONENT_FIELDS, in label order."""
     import numpy as np
 
-    h, w = labels.shape
-    ws = _workspace(ccl_stats_workspace_bytes(h, w), labels.device)
-    _, ncomps = ccl_component_stats(labels, 0, ws=ws)         # the count first
+    _, ncomps = ccl_component_stats(labels, 0)         # the count first
     n = int(ncomps.item())
-    comps, ncomps = ccl_component_stats(labels, n, ws=ws)     # then the records
+    comps, ncomps = ccl_component_stats(labels, n)     # then the records
     ccl_sync()
     raw = comps[:n].cpu().numpy()
     out = {f: raw[:, k].astype(np.int64) for k, f in enumerate(COMPONENT_FIELDS[:6])}
