@@ -94,14 +94,17 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# the sources of the profiled kernels (k_merge, k_seams, k_link and their launch)
+PROFILED_SOURCES = ("ccl_core.cuh", "ccl_tile.cuh", "ccl_plain.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1708_08180_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode())
-                h.update(f.read())
+    for name in PROFILED_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
