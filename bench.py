@@ -471,6 +471,31 @@ def stats_leg(labels, stream, reps: int = 50):
             "what": "pixel count, bounding box and coordinate sums of every component"}
 
 
+def regions_leg(img, out, ws, stream, reps: int = 50):
+    """ccl_label_regions on the headline image with levels {0, 1}: every
+    region, background included (one three-phase pass per level).  Device
+    time per call (CUDA events, after warm-up) and its pixel rate."""
+    import torch
+
+    import paper_1708_08180_gb300 as ccl
+
+    h, w = img.shape
+    for _ in range(3):
+        ccl.ccl_label_regions(img, (0, 1), CONN, out=out, ws=ws, stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ccl.ccl_label_regions(img, (0, 1), CONN, out=out, ws=ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ccl.ccl_sync(stream)
+    ms = e0.elapsed_time(e1) / reps
+    return {"levels": [0, 1], "ms": round(ms, 5), "gpix_s": round(h * w / (ms / 1e3) / 1e9, 2),
+            "gpu_launches_per_call": 6,
+            "what": "every equal-value region (foreground and background) of the headline image"}
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -608,6 +633,9 @@ def run_ours(args, rank, world, local):
         line["e2e"] = e2e_server(host_imgs[0], K, local)
     if rank == 0 and not args.no_stats:
         line["component_stats"] = stats_leg(outs[0], stream)
+    if rank == 0 and not args.no_regions:
+        line["label_regions"] = regions_leg(imgs[1 % ROTATE], outs[1 % ROTATE], wss[1 % ROTATE],
+                                            stream)
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_vs_plain(local)
     if rank == 0 and not args.no_served:
@@ -632,6 +660,8 @@ def main(argv=None) -> int:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stats", action="store_true", help="skip the component-statistics leg")
+    ap.add_argument("--no-regions", action="store_true",
+                    help="skip the every-region (levels 0 and 1) leg")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-vs-plain leg (256 images of 64..2048)")
     ap.add_argument("--no-served", action="store_true",

@@ -129,6 +129,24 @@ ccl_status ccl_label_tiled(const uint8_t *d_img, int32_t *d_labels, int height, 
                            int connectivity, int tile_w, unsigned flags, void *d_ws,
                            size_t ws_bytes, ccl_stream stream);
 
+/* Label every region of a multi-level image: pixels are connected when they
+ * are neighbours and hold the same byte value, which is the predicate the
+ * paper's kernels test (equal dBuff values in Kernel 1, §II-A; equal image
+ * values in Kernel 2, §II-B) before its pseudo-code is specialised to binary
+ * images.  Every pixel whose value is in levels[0..nlevels) gets 1 + the
+ * smallest raster index of its equal-value component; every other pixel 0.
+ * For a binary image, levels = {0, 1} labels background regions too.
+ *   d_img, d_labels, d_ws, ws_bytes, stream : as ccl_label (the workspace
+ *              need is ccl_workspace_bytes(), independent of nlevels)
+ *   levels   : host, nlevels distinct byte values (read during the call only)
+ *   nlevels  : 1..256
+ * Runs one three-phase pass per level on `stream`; the first pass writes
+ * every pixel, later ones only their own.  CCL_ERR_INVALID_ARG on a NULL or
+ * empty level list or a repeated level; otherwise as ccl_label. */
+ccl_status ccl_label_regions(const uint8_t *d_img, int32_t *d_labels, int height, int width,
+                             int connectivity, const uint8_t *levels, int nlevels, void *d_ws,
+                             size_t ws_bytes, ccl_stream stream);
+
 /* Number of unordered pairs of neighbouring pixels that lie in different
  * tiles for this size, connectivity and tile (tile_w x tile_h): the cells the
  * boundary analysis inspects (§II-B; Eq. 1-2 count them for a whole-tile grid).

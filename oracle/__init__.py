@@ -22,6 +22,12 @@ Functions
   * ``seam_pairs(h, w, conn, tile_w, tile_h)`` -- the cross-tile adjacent pixel
     pairs the boundary analysis must union (§II-B, Eq. 1-2), enumerated one by
     one.
+  * ``label_regions(img, levels, conn)`` -- every equal-value region whose
+    value is in ``levels`` (the equality predicate the paper's kernels test,
+    §II-A and §II-B), background included when 0 is listed: the sum over the
+    levels of ``label`` applied to the level's indicator image.
+  * ``label_regions_py(img, levels, conn)`` -- a pure-Python equal-value flood
+    fill for tiny inputs.
   * ``component_stats(labels)`` -- per component of a canonical label image:
     pixel count, inclusive bounding box and coordinate sums (the size and
     location of each region, §I), by definition, in label order.
@@ -132,6 +138,56 @@ def label_py(img, conn: int = 8) -> np.ndarray:
                 for dx, dy in _offsets(conn):
                     qx, qy = x + dx, y + dy
                     if 0 <= qx < w and 0 <= qy < h and img[qy, qx] != 0 and out[qy, qx] == 0:
+                        out[qy, qx] = lab
+                        queue.append((qx, qy))
+    return out
+
+
+def _check_levels(levels) -> list:
+    lv = [int(v) for v in levels]
+    if not lv or len(set(lv)) != len(lv) or any(v < 0 or v > 255 for v in lv):
+        raise ValueError("levels must be distinct byte values")
+    return lv
+
+
+def label_regions(img: np.ndarray, levels, conn: int = 8) -> np.ndarray:
+    """Canonical labels of every equal-value region of ``img`` whose value is in
+    ``levels``; 0 for pixels of other values.
+
+    The paper's kernels join neighbours whose image values are equal (Kernel 1's
+    row and column scans, §II-A; Kernel 2's boundary tests, §II-B).  Regions of
+    different values are disjoint, so the result is the sum over the levels of
+    the canonical labelling of the indicator image ``img == v``."""
+    lv = _check_levels(levels)
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    out = np.zeros(img.shape, dtype=np.int32)
+    for v in lv:
+        out += label((img == v).astype(np.uint8), conn)
+    return out
+
+
+def label_regions_py(img, levels, conn: int = 8) -> np.ndarray:
+    """Pure-Python twin of ``label_regions``: raster scan, and a breadth-first
+    flood fill over neighbours holding the same value as the seed."""
+    _check_conn(conn)
+    lv = set(_check_levels(levels))
+    img = np.asarray(img)
+    h, w = img.shape
+    out = np.zeros((h, w), dtype=np.int32)
+    for y0 in range(h):
+        for x0 in range(w):
+            v = int(img[y0, x0])
+            if v not in lv or out[y0, x0] != 0:
+                continue
+            lab = 1 + y0 * w + x0
+            out[y0, x0] = lab
+            queue = deque([(x0, y0)])
+            while queue:
+                x, y = queue.popleft()
+                for dx, dy in _offsets(conn):
+                    qx, qy = x + dx, y + dy
+                    if 0 <= qx < w and 0 <= qy < h and int(img[qy, qx]) == v \
+                            and out[qy, qx] == 0:
                         out[qy, qx] = lab
                         queue.append((qx, qy))
     return out

@@ -26,6 +26,7 @@ __all__ = [
     "ccl_shutdown", "ccl_status_string", "ccl_set_phase_events", "ccl_label_static", "Server",
     "ccl_get_tile_table", "ccl_set_tile_table", "ccl_autotune", "load",
     "ccl_stats_workspace_bytes", "ccl_component_stats", "component_stats", "COMPONENT_FIELDS",
+    "ccl_label_regions", "label_regions",
 ]
 
 # ccl_component as int32 words: label, count, xmin, ymin, xmax, ymax, then the
@@ -122,6 +123,42 @@ def ccl_label(img, conn: int = 8, out=None, ws=None, stream=None):
                               ws.numel(), _stream_handle(stream))
     check(st, "ccl_label")
     return out
+
+
+def ccl_label_regions(img, levels: Sequence[int], conn: int = 8, out=None, ws=None,
+                      stream=None):
+    """Label every equal-value region of ``img`` whose byte value is in
+    ``levels`` (distinct values 0..255): 1 + the smallest raster index of the
+    region, 0 for pixels of other values.  One three-phase pass per level on
+    ``stream``; ``ws`` as for ``ccl_label``."""
+    torch = _torch()
+    _check_img(img)
+    h, w = img.shape
+    lv = [int(v) for v in levels]
+    if not lv or any(v < 0 or v > 255 for v in lv):
+        raise ValueError("levels must be 1..256 byte values")
+    if out is None:
+        out = torch.empty((h, w), dtype=torch.int32, device=img.device)
+    elif out.dtype != torch.int32 or tuple(out.shape) != (h, w) or not out.is_contiguous():
+        raise TypeError("out must be a contiguous int32 tensor shaped like img")
+    need = ccl_workspace_bytes(h, w, conn)
+    if need == 0:
+        raise CclError(1, "ccl_workspace_bytes")
+    if ws is None:
+        ws = _workspace(need, img.device)
+    host_levels = (ctypes.c_uint8 * len(lv))(*lv)
+    with torch.cuda.device(img.device):
+        st = load().ccl_label_regions(img.data_ptr(), out.data_ptr(), h, w, conn,
+                                      ctypes.addressof(host_levels), len(lv), ws.data_ptr(),
+                                      ws.numel(), _stream_handle(stream))
+    check(st, "ccl_label_regions")
+    return out
+
+
+def label_regions(img, levels: Sequence[int] = (0, 1), conn: int = 8):
+    """Every region of ``img`` whose value is in ``levels``, background
+    included when 0 is listed (see ``ccl_label_regions``)."""
+    return ccl_label_regions(img, levels, conn)
 
 
 def ccl_label_static(img, conn: int = 8, out=None, stream=None):

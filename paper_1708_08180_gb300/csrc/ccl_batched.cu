@@ -335,6 +335,8 @@ static ccl_status enqueue_batched(const ccl_image *imgs, int n, int conn, void *
         b.a.aligned16 = (g.W % 16 == 0) && (reinterpret_cast<uintptr_t>(imgs[k].d_img) % 16 == 0);
         b.a.out_aligned16 =
             (g.W % 4 == 0) && (reinterpret_cast<uintptr_t>(imgs[k].d_labels) % 16 == 0);
+        b.a.level = -1;
+        b.a.merge_out = 0;
         b.tile_off = tiles;
         b.chunk_off = chunks;
         tiles += g.tiles_x * g.tiles_y;

@@ -184,37 +184,48 @@ __device__ __forceinline__ uint32_t nz16(uint4 v) {
 }
 
 // Foreground bits of pixels [gx, gx + n) of row y (n = min(32, W - gx)),
-// bit k = pixel gx + k.  img_end bounds every byte read.
+// bit k = pixel gx + k.  level < 0: foreground = nonzero byte; level in
+// [0, 255]: foreground = byte equal to level (a byte equals the level iff
+// its XOR with the level is zero).  img_end bounds every byte read.
 __device__ __forceinline__ uint32_t load_row_bits(const uint8_t *__restrict__ img,
                                                   const uint8_t *img_end, int y, int gx,
-                                                  int W, bool aligned16) {
+                                                  int W, bool aligned16, int level = -1) {
     int n = W - gx;
     if (n > 32) n = 32;
+    const uint32_t rep = level < 0 ? 0u : (uint32_t)level * 0x01010101u;
     const uint8_t *p = img + (size_t)y * (size_t)W + (size_t)gx;
+    uint32_t bits;
     if (aligned16) {
         // W % 16 == 0 and 16-byte aligned base: n is 16 or 32
-        uint32_t bits = nz16(__ldg(reinterpret_cast<const uint4 *>(p)));
-        if (n > 16) bits |= nz16(__ldg(reinterpret_cast<const uint4 *>(p + 16))) << 16;
-        return bits;
-    }
-    uintptr_t a = reinterpret_cast<uintptr_t>(p);
-    int off = (int)(a & 3u);
-    const uint8_t *wb = p - off;
-    int nwords = (off + n + 3) >> 2;
-    uint64_t acc = 0;
-    for (int k = 0; k < nwords; ++k) {
-        const uint8_t *q = wb + 4 * k;
-        uint32_t m4;
-        if (q >= img && q + 4 <= img_end) {
-            m4 = nz4(__ldg(reinterpret_cast<const uint32_t *>(q)));
-        } else {
-            m4 = 0;
-            for (int b = 0; b < 4; ++b)
-                if (q + b >= img && q + b < img_end && q[b] != 0) m4 |= 1u << b;
+        uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        v.x ^= rep; v.y ^= rep; v.z ^= rep; v.w ^= rep;
+        bits = nz16(v);
+        if (n > 16) {
+            uint4 u = __ldg(reinterpret_cast<const uint4 *>(p + 16));
+            u.x ^= rep; u.y ^= rep; u.z ^= rep; u.w ^= rep;
+            bits |= nz16(u) << 16;
         }
-        acc |= (uint64_t)m4 << (4 * k);
+    } else {
+        uintptr_t a = reinterpret_cast<uintptr_t>(p);
+        int off = (int)(a & 3u);
+        const uint8_t *wb = p - off;
+        int nwords = (off + n + 3) >> 2;
+        uint64_t acc = 0;
+        for (int k = 0; k < nwords; ++k) {
+            const uint8_t *q = wb + 4 * k;
+            uint32_t m4;
+            if (q >= img && q + 4 <= img_end) {
+                m4 = nz4(__ldg(reinterpret_cast<const uint32_t *>(q)) ^ rep);
+            } else {
+                m4 = 0;
+                for (int b = 0; b < 4; ++b)
+                    if (q + b >= img && q + b < img_end && (q[b] ^ (rep & 0xFFu)) != 0) m4 |= 1u << b;
+            }
+            acc |= (uint64_t)m4 << (4 * k);
+        }
+        bits = (uint32_t)(acc >> off);
     }
-    uint32_t bits = (uint32_t)(acc >> off);
+    if (level >= 0) bits = ~bits;   // nonzero XOR = not equal to the level
     return n == 32 ? bits : (bits & ((1u << n) - 1u));
 }
 

@@ -56,8 +56,10 @@ inline cudaError_t launch_pdl(void (*kernel)(P...), unsigned grid, unsigned bloc
 void free_batched_state();
 
 // Enqueue the three single-image kernels with the given workspace (ccl_plain.cu).
+// level < 0: foreground = nonzero byte, else byte == level; merge_out: the
+// link phase writes only this pass's foreground pixels.
 ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, int width,
                          int conn, int tile_w, unsigned flags, void *d_ws, size_t ws_bytes,
-                         cudaStream_t stream);
+                         cudaStream_t stream, int level = -1, bool merge_out = false);
 
 }  // namespace ccl

@@ -135,7 +135,7 @@ static thread_local bool t_phase_armed = false;
 
 ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, int width,
                          int conn, int tile_w, unsigned flags, void *d_ws, size_t ws_bytes,
-                         cudaStream_t stream) {
+                         cudaStream_t stream, int level, bool merge_out) {
     if (!d_img || !d_labels || !valid_image_dims(height, width) || !valid_conn(conn))
         return CCL_ERR_INVALID_ARG;
     const bool default_tile = tile_w == 0;
@@ -165,6 +165,8 @@ ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, in
     a.g = g;
     a.aligned16 = (width % 16 == 0) && (reinterpret_cast<uintptr_t>(d_img) % 16 == 0);
     a.out_aligned16 = (width % 4 == 0) && (reinterpret_cast<uintptr_t>(d_labels) % 16 == 0);
+    a.level = level;
+    a.merge_out = merge_out ? 1 : 0;
     const bool local_only = (flags & CCL_FLAG_LOCAL_ONLY) != 0;
 
     const bool timed = t_phase_armed;
@@ -221,6 +223,27 @@ extern "C" ccl_status ccl_label(const uint8_t *d_img, int32_t *d_labels, int hei
                                 ccl_stream stream) {
     return ccl::enqueue_label(d_img, d_labels, height, width, connectivity, 0, 0u, d_ws,
                               ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" ccl_status ccl_label_regions(const uint8_t *d_img, int32_t *d_labels, int height,
+                                        int width, int connectivity, const uint8_t *levels,
+                                        int nlevels, void *d_ws, size_t ws_bytes,
+                                        ccl_stream stream) {
+    if (!levels || nlevels < 1 || nlevels > 256) return CCL_ERR_INVALID_ARG;
+    bool seen[256] = {};
+    for (int k = 0; k < nlevels; ++k) {
+        if (seen[levels[k]]) return CCL_ERR_INVALID_ARG;   // levels must be distinct
+        seen[levels[k]] = true;
+    }
+    // one pass per level: the first writes every pixel, the others only theirs
+    for (int k = 0; k < nlevels; ++k) {
+        const ccl_status st = ccl::enqueue_label(d_img, d_labels, height, width, connectivity, 0,
+                                                 0u, d_ws, ws_bytes,
+                                                 reinterpret_cast<cudaStream_t>(stream),
+                                                 (int)levels[k], k > 0);
+        if (st != CCL_OK) return st;
+    }
+    return CCL_OK;
 }
 
 extern "C" ccl_status ccl_label_tiled(const uint8_t *d_img, int32_t *d_labels, int height,

@@ -10,12 +10,14 @@ namespace ccl {
 // One image as the kernels see it.
 struct ImageArgs {
     const uint8_t *img;
-    int32_t *labels;       // output, also the global union-find array
+    int32_t *labels;       // output label image (written by the link phase only)
     uint32_t *bits;        // bit image: H rows x nwg words
     int *tws;              // per-tile workspace, g.tile_ints ints per tile
     Geom g;
     int aligned16;         // image rows start on 16-byte boundaries (W % 16 == 0)
     int out_aligned16;     // label rows start on 16-byte boundaries (W % 4 == 0)
+    int level;             // -1: foreground = nonzero byte; else byte == level
+    int merge_out;         // link writes only its foreground pixels, keeping the others
 };
 
 // Shared memory of the local-merge phase.
@@ -82,7 +84,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     for (int j = 0; j < HS; ++j) {
         const int y = y0 + s * HS + j;
         rows[j] = (y < g.H && gx < g.W)
-                      ? load_row_bits(a.img, img_end, y, gx, g.W, a.aligned16 != 0)
+                      ? load_row_bits(a.img, img_end, y, gx, g.W, a.aligned16 != 0, a.level)
                       : 0u;
         if (y < g.H && (x0 / 32 + w) < g.nwg)
             st_policy(a.bits + (size_t)y * g.nwg + (x0 / 32 + w), rows[j], l2_evict_last());
@@ -752,13 +754,17 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
             const uint32_t rb = sm.rows[r * NW + wq];
             const uint32_t sq = sm.st[o];
             int cur = sm.base[o] + __popc(sq & le_mask(b0)) - 1;
-            int v[4];
+            int32_t *out = a.labels + (size_t)(y0 + r) * g.W + x0 + c0;
+            int v[4] = {0, 0, 0, 0};
+            if (a.merge_out) {   // keep the pixels this pass does not label
+                const int4 keep = *reinterpret_cast<const int4 *>(out);
+                v[0] = keep.x; v[1] = keep.y; v[2] = keep.z; v[3] = keep.w;
+            }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (e > 0) cur += (sq >> (b0 + e)) & 1u;
-                v[e] = ((rb >> (b0 + e)) & 1u) ? sm.S[cur < 0 ? 0 : cur] : 0;
+                if ((rb >> (b0 + e)) & 1u) v[e] = sm.S[cur < 0 ? 0 : cur];
             }
-            int32_t *out = a.labels + (size_t)(y0 + r) * g.W + x0 + c0;
             __stcs(reinterpret_cast<int4 *>(out), make_int4(v[0], v[1], v[2], v[3]));
         }
     } else {
@@ -770,7 +776,9 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
             const uint32_t rb = sm.rows[r * NW + wq];
             const uint32_t sq = sm.st[o];
             const int cur = sm.base[o] + __popc(sq & le_mask(b)) - 1;
-            a.labels[(size_t)(y0 + r) * g.W + x0 + c] = ((rb >> b) & 1u) ? sm.S[cur < 0 ? 0 : cur] : 0;
+            int32_t *out = a.labels + (size_t)(y0 + r) * g.W + x0 + c;
+            if ((rb >> b) & 1u) *out = sm.S[cur < 0 ? 0 : cur];
+            else if (!a.merge_out) *out = 0;
         }
     }
 }

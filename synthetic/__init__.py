@@ -53,6 +53,21 @@ def block_noise(h: int, w: int, g: int, seed: int, p: float = 0.5) -> np.ndarray
     return np.ascontiguousarray(np.repeat(np.repeat(cells, g, axis=0), g, axis=1)[:h, :w])
 
 
+CFG_LEVELS = 5      # multi-level images
+
+
+def multilevel(h: int, w: int, values, seed: int, g: int = 1) -> np.ndarray:
+    """Each g x g cell takes one of ``values`` (bytes) uniformly at random;
+    g = 1 is i.i.d. per pixel, larger g gives blobby regions of equal value."""
+    vals = np.asarray(list(values), dtype=np.uint8)
+    rng = rng_for(CFG_LEVELS, seed * 1000 + g * 7 + vals.size, h, w, 0.0)
+    ch, cw = -(-h // g), -(-w // g)
+    cells = vals[rng.integers(0, vals.size, size=(ch, cw))]
+    if g == 1:
+        return np.ascontiguousarray(cells)
+    return np.ascontiguousarray(np.repeat(np.repeat(cells, g, axis=0), g, axis=1)[:h, :w])
+
+
 def serpentine(h: int, w: int, transpose: bool = False) -> np.ndarray:
     """One 1-pixel-wide path: rows y = 0 (mod 2) fully set, row y = 1 (mod 4)
     only at x = W-1, row y = 3 (mod 4) only at x = 0."""

@@ -38,7 +38,32 @@ def load_golden(name: str) -> dict:
 
 
 def golden_names():
-    return sorted(n for n in os.listdir(GOLDEN) if n.endswith(".txt") and n != "README.txt")
+    return sorted(n for n in os.listdir(GOLDEN) if n.endswith(".txt") and n != "README.txt"
+                  and not n.startswith("regions_"))
+
+
+def regions_golden_names():
+    return sorted(n for n in os.listdir(GOLDEN) if n.startswith("regions_"))
+
+
+def load_regions_golden(name: str) -> dict:
+    """Parse a hand-worked multi-level fixture: blocks "image:", "levels:",
+    "conn4:", "conn8:"."""
+    blocks, cur = {}, None
+    with open(os.path.join(GOLDEN, name)) as f:
+        for raw in f:
+            line = raw.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.endswith(":"):
+                cur = line[:-1]
+                blocks[cur] = []
+                continue
+            blocks[cur].append([int(v) for v in line.split()])
+    return {"image": np.array(blocks["image"], dtype=np.uint8),
+            "levels": [v for row in blocks["levels"] for v in row],
+            "conn4": np.array(blocks["conn4"], dtype=np.int64),
+            "conn8": np.array(blocks["conn8"], dtype=np.int64)}
 
 
 def all_images(h: int, w: int) -> np.ndarray:
@@ -75,6 +100,39 @@ def closure_labels(imgs: np.ndarray, conn: int) -> np.ndarray:
     first = np.argmax(r > 0, axis=2)
     lab = np.where(fg, first + 1, 0)
     return lab.reshape(cnt, h, w).astype(np.int32)
+
+
+def closure_labels_valued(imgs: np.ndarray, conn: int, levels) -> np.ndarray:
+    """Canonical region labels by transitive closure, for multi-level images:
+    R starts as (adjacent or equal) and (equal value) and (value in levels),
+    and is squared until it stops changing; pixel i's label is 1 + the first j
+    reachable from it, 0 for a value not in levels."""
+    cnt, h, w = imgs.shape
+    n = h * w
+    ys, xs = np.divmod(np.arange(n), w)
+    dy = np.abs(ys[:, None] - ys[None, :])
+    dx = np.abs(xs[:, None] - xs[None, :])
+    adj = ((dx + dy) <= 1) if conn == 4 else (np.maximum(dx, dy) <= 1)
+    v = imgs.reshape(cnt, n).astype(np.int64)
+    keep = np.isin(v, np.asarray(list(levels), dtype=np.int64))
+    r = (adj[None] & (v[:, :, None] == v[:, None, :]) & keep[:, :, None]).astype(np.float32)
+    for _ in range(max(1, int(np.ceil(np.log2(max(n, 2)))) + 1)):
+        r2 = (np.matmul(r, r) > 0).astype(np.float32)
+        if np.array_equal(r2, r):
+            break
+        r = r2
+    first = np.argmax(r > 0, axis=2)
+    lab = np.where(keep, first + 1, 0)
+    return lab.reshape(cnt, h, w).astype(np.int32)
+
+
+def all_images_valued(h: int, w: int, nval: int) -> np.ndarray:
+    """Every h x w image over the values 0..nval-1 (image k: pixel i = digit i
+    of k in base nval)."""
+    n = h * w
+    k = np.arange(nval ** n, dtype=np.int64)
+    digits = (k[:, None] // (nval ** np.arange(n))[None, :]) % nval
+    return digits.reshape(-1, h, w).astype(np.uint8)
 
 
 def two_pass_count(img: np.ndarray, conn: int) -> int:

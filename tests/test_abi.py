@@ -98,6 +98,21 @@ def test_host_validation_rejects_before_enqueueing(lib):
     need = ccl.ccl_workspace_bytes(64, 64, 8)
     assert lib.ccl_label(P(256), P(512), 64, 64, 8, P(4096), need - 1, None) == _lib.CCL_ERR_INVALID_ARG
     assert lib.ccl_label(P(256), P(512), 64, 64, 8, P(4096 + 16), need, None) == _lib.CCL_ERR_INVALID_ARG
+    # every-region labelling: the level list is checked first, then the image
+    lv = (ctypes.c_uint8 * 3)(0, 1, 1)
+    addr = ctypes.addressof(lv)
+    assert lib.ccl_label_regions(P(256), P(512), 4, 4, 8, None, 1, None, 0, None) == \
+        _lib.CCL_ERR_INVALID_ARG
+    assert lib.ccl_label_regions(P(256), P(512), 4, 4, 8, addr, 0, None, 0, None) == \
+        _lib.CCL_ERR_INVALID_ARG
+    assert lib.ccl_label_regions(P(256), P(512), 4, 4, 8, addr, 257, None, 0, None) == \
+        _lib.CCL_ERR_INVALID_ARG
+    assert lib.ccl_label_regions(P(256), P(512), 4, 4, 8, addr, 3, None, 0, None) == \
+        _lib.CCL_ERR_INVALID_ARG                                  # level 1 repeated
+    assert lib.ccl_label_regions(None, P(512), 4, 4, 8, addr, 2, None, 0, None) == \
+        _lib.CCL_ERR_INVALID_ARG
+    assert lib.ccl_label_regions(P(256), P(512), 4, 4, 6, addr, 2, None, 0, None) == \
+        _lib.CCL_ERR_INVALID_ARG
     arr = (_lib.ccl_image * 1)()
     assert lib.ccl_label_batched(arr, 1, 8, None, 0, None) == _lib.CCL_ERR_INVALID_ARG
     assert lib.ccl_label_batched(arr, 0, 8, None, 0, None) == _lib.CCL_ERR_INVALID_ARG

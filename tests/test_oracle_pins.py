@@ -10,8 +10,9 @@ import pytest
 
 import oracle
 import synthetic
-from helpers import (all_images, canonical_from_arbitrary, check_invariants,
-                     closure_labels, golden_names, load_golden, scipy_canonical,
+from helpers import (all_images, all_images_valued, canonical_from_arbitrary,
+                     check_invariants, closure_labels, closure_labels_valued, golden_names,
+                     load_golden, load_regions_golden, regions_golden_names, scipy_canonical,
                      two_pass_count)
 
 SIZES_4x4 = [(h, w) for h in range(1, 5) for w in range(1, 5)]
@@ -246,3 +247,86 @@ def test_component_stats_closed_forms():
     assert oracle.component_stats(oracle.label(synthetic.empty(h, w), 4))["count"].size == 0
     cb = oracle.component_stats(oracle.label(synthetic.checkerboard(h, w), 4))
     assert cb["count"].size == h * w // 2 and set(cb["count"].tolist()) == {1}
+
+
+# ---------------------------------------------------------------------------
+# label_regions: every equal-value region (the paper's equality predicate,
+# §II-A row/column scans and §II-B boundary tests)
+
+@pytest.mark.parametrize("name", regions_golden_names())
+@pytest.mark.parametrize("conn", [4, 8])
+def test_regions_hand_worked(name, conn):
+    g = load_regions_golden(name)
+    np.testing.assert_array_equal(oracle.label_regions(g["image"], g["levels"], conn),
+                                  g[f"conn{conn}"])
+    np.testing.assert_array_equal(oracle.label_regions_py(g["image"], g["levels"], conn),
+                                  g[f"conn{conn}"])
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("hw", [(1, 4), (2, 2), (2, 3), (3, 2), (1, 6)],
+                         ids=lambda s: f"{s[0]}x{s[1]}")
+def test_regions_closure_all_three_level_images(hw, conn):
+    """Every image over {0, 1, 2} of the size, all values and a subset labelled."""
+    h, w = hw
+    imgs = all_images_valued(h, w, 3)
+    for levels in ([0, 1, 2], [2, 0], [1]):
+        want = closure_labels_valued(imgs, conn, levels)
+        for k in range(imgs.shape[0]):
+            got = oracle.label_regions(imgs[k], levels, conn)
+            if not np.array_equal(got, want[k]):
+                raise AssertionError(f"image {k} levels {levels}: {got} vs {want[k]}")
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_regions_python_twin_and_scipy(conn):
+    rng = np.random.default_rng(11)
+    for t in range(24):
+        h, w = (int(v) for v in rng.integers(1, 30, size=2))
+        nval = int(rng.integers(2, 6))
+        vals = rng.choice(256, size=nval, replace=False)
+        img = synthetic.multilevel(h, w, vals, t, g=int(rng.integers(1, 4)))
+        levels = list(rng.permutation(vals)[: int(rng.integers(1, nval + 1))])
+        got = oracle.label_regions(img, levels, conn)
+        np.testing.assert_array_equal(oracle.label_regions_py(img, levels, conn), got)
+        # per level, scipy's labelling of the indicator image, canonicalised
+        want = np.zeros(img.shape, np.int64)
+        for v in levels:
+            want += scipy_canonical(img == v, conn)
+        np.testing.assert_array_equal(got, want)
+
+
+def test_regions_reduce_to_binary_labelling():
+    """On a binary image, labelling the nonzero level alone is the plain
+    labelling, and labelling {0, v} adds the background regions of the
+    complement image without touching the foreground labels."""
+    for conn in (4, 8):
+        for seed in range(6):
+            img = synthetic.bernoulli(37 + seed, 53, 0.3 + 0.08 * seed, seed, cfg_id=12,
+                                      fg=255 if seed % 2 else 1)
+            v = int(img.max()) or 1
+            plain = oracle.label(img, conn)
+            np.testing.assert_array_equal(oracle.label_regions(img, [v], conn), plain)
+            both = oracle.label_regions(img, [0, v], conn)
+            np.testing.assert_array_equal(both[img != 0], plain[img != 0])
+            comp = (img == 0).astype(np.uint8)
+            np.testing.assert_array_equal(both[img == 0], oracle.label(comp, conn)[img == 0])
+            assert (both > 0).all()
+
+
+def test_regions_level_order_irrelevant_and_bad_levels():
+    img = synthetic.multilevel(40, 41, [3, 9, 200], 1, g=2)
+    a = oracle.label_regions(img, [3, 9, 200], 8)
+    np.testing.assert_array_equal(oracle.label_regions(img, [200, 3, 9], 8), a)
+    for bad in ([], [1, 1], [256], [-1]):
+        with pytest.raises(ValueError):
+            oracle.label_regions(img, bad, 8)
+
+
+def test_regions_catch_a_planted_mistake():
+    """A labelling that ignores the value (joins neighbours of any two listed
+    levels) fails the closure pin: the pin can see the mistake."""
+    imgs = all_images_valued(2, 2, 3)
+    want = closure_labels_valued(imgs, 4, [1, 2])
+    wrong = np.stack([oracle.label(np.isin(im, [1, 2]).astype(np.uint8), 4) for im in imgs])
+    assert not np.array_equal(wrong, want)
