@@ -28,6 +28,9 @@ Functions
     levels of ``label`` applied to the level's indicator image.
   * ``label_regions_py(img, levels, conn)`` -- a pure-Python equal-value flood
     fill for tiny inputs.
+  * ``label3d(vol, conn)`` / ``label3d_py`` -- the same definition for 3-D
+    volumes (the "2D/3D grid" of §I), 6-, 18- or 26-connectivity: the C flood
+    fill and a pure-Python twin.
   * ``component_stats(labels)`` -- per component of a canonical label image:
     pixel count, inclusive bounding box and coordinate sums (the size and
     location of each region, §I), by definition, in label order.
@@ -73,6 +76,10 @@ def _load():
                 fn.restype = ctypes.c_int
                 fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                ctypes.c_int64, ctypes.c_int]
+            fn = lib.ccl_oracle_bfs3d
+            fn.restype = ctypes.c_int
+            fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                           ctypes.c_int64, ctypes.c_int]
             fn = lib.ccl_oracle_bfs_many
             fn.restype = ctypes.c_int
             fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
@@ -190,6 +197,56 @@ def label_regions_py(img, levels, conn: int = 8) -> np.ndarray:
                             and out[qy, qx] == 0:
                         out[qy, qx] = lab
                         queue.append((qx, qy))
+    return out
+
+
+def _offsets3(conn: int):
+    if conn not in (6, 18, 26):
+        raise ValueError(f"3-D connectivity must be 6, 18 or 26, got {conn}")
+    lim = {6: 1, 18: 2, 26: 3}[conn]
+    return tuple((dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                 if 0 < abs(dx) + abs(dy) + abs(dz) <= lim)
+
+
+def label3d(vol: np.ndarray, conn: int = 26) -> np.ndarray:
+    """Canonical labels of a 3-D uint8 volume (nonzero = foreground), indexed
+    ``vol[z, y, x]``, voxel index ``(z*H + y)*W + x``: 0 for background, 1 +
+    the smallest index of the voxel's component.  ``conn``: 6 (faces), 18
+    (faces and edges) or 26 (faces, edges and corners)."""
+    _offsets3(conn)
+    vol = np.ascontiguousarray(vol, dtype=np.uint8)
+    if vol.ndim != 3 or min(vol.shape) < 1:
+        raise ValueError("vol must be a non-empty 3-D array")
+    out = np.empty(vol.shape, dtype=np.int32)
+    rc = _load().ccl_oracle_bfs3d(vol.ctypes.data, out.ctypes.data, vol.shape[0], vol.shape[1],
+                                  vol.shape[2], conn)
+    if rc != 0:
+        raise RuntimeError(f"oracle failed with code {rc}")
+    return out
+
+
+def label3d_py(vol, conn: int = 26) -> np.ndarray:
+    """Pure-Python twin of ``label3d`` for tiny volumes."""
+    offs = _offsets3(conn)
+    vol = np.asarray(vol)
+    d, h, w = vol.shape
+    out = np.zeros((d, h, w), dtype=np.int32)
+    for z0 in range(d):
+        for y0 in range(h):
+            for x0 in range(w):
+                if vol[z0, y0, x0] == 0 or out[z0, y0, x0] != 0:
+                    continue
+                lab = 1 + (z0 * h + y0) * w + x0
+                out[z0, y0, x0] = lab
+                queue = deque([(x0, y0, z0)])
+                while queue:
+                    x, y, z = queue.popleft()
+                    for dx, dy, dz in offs:
+                        qx, qy, qz = x + dx, y + dy, z + dz
+                        if 0 <= qx < w and 0 <= qy < h and 0 <= qz < d \
+                                and vol[qz, qy, qx] != 0 and out[qz, qy, qx] == 0:
+                            out[qz, qy, qx] = lab
+                            queue.append((qx, qy, qz))
     return out
 
 

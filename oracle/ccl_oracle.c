@@ -113,3 +113,73 @@ int ccl_oracle_bfs_many(const uint8_t *imgs, int32_t *outs, int64_t count,
     }
     return ORACLE_OK;
 }
+
+/*
+ * Volumes (the "2D/3D grid" the paper's introduction names, §I): the same
+ * definition one dimension up.  vol: d*h*w bytes, index i = (z*h + y)*w + x,
+ * nonzero = foreground; out[i] = 0 for background, else 1 + the smallest index
+ * of i's component.  Connectivity: 6 (face neighbours, |dx|+|dy|+|dz| = 1),
+ * 18 (faces and edges, |dx|+|dy|+|dz| <= 2) or 26 (max(|dx|,|dy|,|dz|) = 1).
+ * Same algorithm: raster scan, breadth-first flood fill from the first
+ * unlabelled foreground voxel.
+ */
+int ccl_oracle_bfs3d(const uint8_t *vol, int32_t *out, int64_t d, int64_t h,
+                     int64_t w, int conn)
+{
+    int off[26][3];
+    int nn = 0, a, b, c;
+    int64_t n, i, head, tail;
+    int32_t *queue;
+
+    if (vol == NULL || out == NULL || d < 1 || h < 1 || w < 1)
+        return ORACLE_EINVAL;
+    if (conn != 6 && conn != 18 && conn != 26)
+        return ORACLE_EINVAL;
+    if (d > (int64_t)2147483646 / h || d * h > (int64_t)2147483646 / w)
+        return ORACLE_EINVAL;
+    n = d * h * w;
+    for (c = -1; c <= 1; ++c)
+        for (b = -1; b <= 1; ++b)
+            for (a = -1; a <= 1; ++a) {
+                int s = abs(a) + abs(b) + abs(c);
+                if (s == 0 || (conn == 6 && s > 1) || (conn == 18 && s > 2))
+                    continue;
+                off[nn][0] = a;
+                off[nn][1] = b;
+                off[nn][2] = c;
+                ++nn;
+            }
+
+    memset(out, 0, (size_t)n * sizeof(int32_t));
+    queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (queue == NULL)
+        return ORACLE_ENOMEM;
+
+    for (i = 0; i < n; ++i) {
+        int32_t label;
+        if (vol[i] == 0 || out[i] != 0)
+            continue;
+        label = (int32_t)(i + 1);
+        out[i] = label;
+        head = 0;
+        tail = 0;
+        queue[tail++] = (int32_t)i;
+        while (head < tail) {
+            int32_t p = queue[head++];
+            int64_t px = p % w, py = (p / w) % h, pz = p / (w * h);
+            int k;
+            for (k = 0; k < nn; ++k) {
+                int64_t qx = px + off[k][0], qy = py + off[k][1], qz = pz + off[k][2], q;
+                if (qx < 0 || qx >= w || qy < 0 || qy >= h || qz < 0 || qz >= d)
+                    continue;
+                q = (qz * h + qy) * w + qx;
+                if (vol[q] == 0 || out[q] != 0)
+                    continue;
+                out[q] = label;
+                queue[tail++] = (int32_t)q;
+            }
+        }
+    }
+    free(queue);
+    return ORACLE_OK;
+}

@@ -68,6 +68,25 @@ def multilevel(h: int, w: int, values, seed: int, g: int = 1) -> np.ndarray:
     return np.ascontiguousarray(np.repeat(np.repeat(cells, g, axis=0), g, axis=1)[:h, :w])
 
 
+CFG_VOLUME = 6      # 3-D volumes
+
+
+def bernoulli3d(d: int, h: int, w: int, p: float, seed: int, g: int = 1) -> np.ndarray:
+    """A d x h x w volume (index [z, y, x]) of i.i.d. Bernoulli(p) voxels, or of
+    Bernoulli(p) g x g x g cells when g > 1 (blobby regions)."""
+    rng = rng_for(CFG_VOLUME, seed * 100 + g, d * h, w, p)
+    cd, ch, cw = -(-d // g), -(-h // g), -(-w // g)
+    out = np.empty((cd, ch, cw), dtype=np.uint8)
+    plane = max(1, (1 << 24) // max(ch * cw, 1))   # bounded float32 scratch
+    for z0 in range(0, cd, plane):
+        z1 = min(cd, z0 + plane)
+        out[z0:z1] = rng.random((z1 - z0, ch, cw), dtype=np.float32) < p
+    if g == 1:
+        return out
+    return np.ascontiguousarray(
+        np.repeat(np.repeat(np.repeat(out, g, axis=0), g, axis=1), g, axis=2)[:d, :h, :w])
+
+
 def serpentine(h: int, w: int, transpose: bool = False) -> np.ndarray:
     """One 1-pixel-wide path: rows y = 0 (mod 2) fully set, row y = 1 (mod 4)
     only at x = W-1, row y = 3 (mod 4) only at x = 0."""
