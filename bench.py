@@ -496,6 +496,41 @@ def regions_leg(img, out, ws, stream, reps: int = 50):
             "what": "every equal-value region (foreground and background) of the headline image"}
 
 
+def volume_leg(dev, stream, reps: int = 20, side: int = 512, p: float = 0.5):
+    """ccl_label3d on a side^3 Bernoulli(p) volume at 6-, 18- and 26-connectivity:
+    device time per call (CUDA events, after warm-up; input 128 MiB and labels
+    512 MiB, both larger than L2) and its voxel rate."""
+    import torch
+
+    import paper_1708_08180_gb300 as ccl
+    import synthetic
+
+    vol = torch.from_numpy(synthetic.bernoulli3d(side, side, side, p, 0)).to(dev)
+    out = torch.empty((side, side, side), dtype=torch.int32, device=dev)
+    res = {"shape": [side, side, side], "density": p,
+           "what": "3-D labelling (bricks of 32x16x16 voxels), labels 1 + smallest voxel index"}
+    for conn in (6, 18, 26):
+        ws = torch.empty(ccl.ccl_workspace_bytes3d(side, side, side, conn), dtype=torch.uint8,
+                         device=dev)
+        for _ in range(3):
+            ccl.ccl_label3d(vol, conn, out=out, ws=ws, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ccl.ccl_label3d(vol, conn, out=out, ws=ws, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ccl.ccl_sync(stream)
+        ms = e0.elapsed_time(e1) / reps
+        peak, _ = hbm_peak()
+        res[f"conn{conn}"] = {"ms": round(ms, 4),
+                              "gvox_s": round(side ** 3 / (ms / 1e3) / 1e9, 2),
+                              "path_frac_5B": round(5 * side ** 3 / (ms / 1e3) / 1e9 / peak, 4)}
+        del ws
+    return res
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -633,6 +668,8 @@ def run_ours(args, rank, world, local):
         line["e2e"] = e2e_server(host_imgs[0], K, local)
     if rank == 0 and not args.no_stats:
         line["component_stats"] = stats_leg(outs[0], stream)
+    if rank == 0 and not args.no_volume:
+        line["volume"] = volume_leg(dev, stream)
     if rank == 0 and not args.no_regions:
         line["label_regions"] = regions_leg(imgs[1 % ROTATE], outs[1 % ROTATE], wss[1 % ROTATE],
                                             stream)
@@ -660,6 +697,7 @@ def main(argv=None) -> int:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stats", action="store_true", help="skip the component-statistics leg")
+    ap.add_argument("--no-volume", action="store_true", help="skip the 3-D volume leg")
     ap.add_argument("--no-regions", action="store_true",
                     help="skip the every-region (levels 0 and 1) leg")
     ap.add_argument("--no-batched", action="store_true",

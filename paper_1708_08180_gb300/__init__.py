@@ -26,7 +26,7 @@ __all__ = [
     "ccl_shutdown", "ccl_status_string", "ccl_set_phase_events", "ccl_label_static", "Server",
     "ccl_get_tile_table", "ccl_set_tile_table", "ccl_autotune", "load",
     "ccl_stats_workspace_bytes", "ccl_component_stats", "component_stats", "COMPONENT_FIELDS",
-    "ccl_label_regions", "label_regions",
+    "ccl_label_regions", "label_regions", "ccl_label3d", "ccl_workspace_bytes3d", "label3d",
 ]
 
 # ccl_component as int32 words: label, count, xmin, ymin, xmax, ymax, then the
@@ -159,6 +159,43 @@ def label_regions(img, levels: Sequence[int] = (0, 1), conn: int = 8):
     """Every region of ``img`` whose value is in ``levels``, background
     included when 0 is listed (see ``ccl_label_regions``)."""
     return ccl_label_regions(img, levels, conn)
+
+
+def ccl_workspace_bytes3d(depth: int, height: int, width: int, conn: int) -> int:
+    return int(load().ccl_workspace_bytes3d(depth, height, width, conn))
+
+
+def ccl_label3d(vol, conn: int = 26, out=None, ws=None, stream=None):
+    """Label a 3-D volume ``vol`` (CUDA uint8, D x H x W, index [z, y, x]) into
+    ``out`` (CUDA int32, same shape): 0 for background, 1 + the smallest voxel
+    index ``(z*H + y)*W + x`` of the component.  ``conn``: 6, 18 or 26.  ``ws``:
+    a CUDA uint8 tensor of at least ``ccl_workspace_bytes3d`` bytes (allocated
+    here when None).  Enqueued on ``stream`` (default: current)."""
+    torch = _torch()
+    if not isinstance(vol, torch.Tensor) or not vol.is_cuda:
+        raise TypeError("volume must be a CUDA tensor")
+    if vol.dtype != torch.uint8 or vol.dim() != 3 or not vol.is_contiguous():
+        raise TypeError("volume must be a contiguous 3-D uint8 tensor")
+    d, h, w = vol.shape
+    if out is None:
+        out = torch.empty((d, h, w), dtype=torch.int32, device=vol.device)
+    elif out.dtype != torch.int32 or tuple(out.shape) != (d, h, w) or not out.is_contiguous():
+        raise TypeError("out must be a contiguous int32 tensor shaped like vol")
+    need = ccl_workspace_bytes3d(d, h, w, conn)
+    if need == 0:
+        raise CclError(1, "ccl_workspace_bytes3d")
+    if ws is None:
+        ws = _workspace(need, vol.device)
+    with torch.cuda.device(vol.device):
+        st = load().ccl_label3d(vol.data_ptr(), out.data_ptr(), d, h, w, conn, ws.data_ptr(),
+                                ws.numel(), _stream_handle(stream))
+    check(st, "ccl_label3d")
+    return out
+
+
+def label3d(vol, conn: int = 26):
+    """Canonical labels of a 3-D volume (see ``ccl_label3d``)."""
+    return ccl_label3d(vol, conn)
 
 
 def ccl_label_static(img, conn: int = 8, out=None, stream=None):

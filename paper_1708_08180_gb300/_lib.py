@@ -58,6 +58,9 @@ _SIGS = {
     "ccl_label_tiled": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint,
                                    _P, _c.c_size_t, _P]),
     "ccl_label_static": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_int, _P]),
+    "ccl_label3d": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _P, _c.c_size_t,
+                               _P]),
+    "ccl_workspace_bytes3d": (_c.c_size_t, [_c.c_int, _c.c_int, _c.c_int, _c.c_int]),
     "ccl_label_regions": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_int, _P, _c.c_int, _P,
                                      _c.c_size_t, _P]),
     "ccl_stats_workspace_bytes": (_c.c_size_t, [_c.c_int, _c.c_int, _c.c_int]),

@@ -19,6 +19,7 @@ LIB = os.path.join(BUILD, "libccl.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["ccl_runtime.cu", "ccl_plain.cu", "ccl_batched.cu", "ccl_noalloc.cu", "ccl_stats.cu",
+                "ccl_volume.cu",
                 "ccl_autotune.cu"]
 CXX_SOURCES = ["ccl_server.cpp"]
 

@@ -323,7 +323,10 @@ struct GlobalForest {
     }
 };
 
-__device__ __forceinline__ gnode gfind(const GlobalForest &F, gnode x, int &budget, int *err) {
+// The walks below take any forest type with `gnode *par(gnode)` (the tiles of
+// an image here; the bricks of a volume in the 3-D path).
+template <class Forest>
+__device__ __forceinline__ gnode gfind(const Forest &F, gnode x, int &budget, int *err) {
     // Walk to the root, remembering the first two nodes passed whose parent
     // is not the root, then point those at the root.  Keys strictly decrease
     // along parent links, so a node seen below the root always has a larger
@@ -348,7 +351,8 @@ __device__ __forceinline__ gnode gfind(const GlobalForest &F, gnode x, int &budg
 
 // Both finds of a union, walked in lock step so their loads overlap (the
 // latency is the longer walk, not the sum); same compression rule as gfind.
-__device__ __forceinline__ void gfind2(const GlobalForest &F, gnode &a, gnode &b, int &budget,
+template <class Forest>
+__device__ __forceinline__ void gfind2(const Forest &F, gnode &a, gnode &b, int &budget,
                                        int *err) {
     gnode ra = a, rb = b;
     gnode prev_a = kNoNode, prev_b = kNoNode, wa = kNoNode, wb = kNoNode;
@@ -384,7 +388,8 @@ __device__ __forceinline__ void gfind2(const GlobalForest &F, gnode &a, gnode &b
     b = rb;
 }
 
-__device__ __forceinline__ void gunion(const GlobalForest &F, gnode a, gnode b, int &budget,
+template <class Forest>
+__device__ __forceinline__ void gunion(const Forest &F, gnode a, gnode b, int &budget,
                                        int *err) {
     if (a == b) return;
     {   // first try, one atomic: hook the larger node under the smaller if it is

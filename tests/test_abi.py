@@ -74,6 +74,14 @@ def test_tile_table_and_workspace_sizes(lib):
     assert ccl.ccl_workspace_bytes(46341, 46341, 8) == 0      # > 2^31 - 2 pixels
     assert ccl.ccl_workspace_bytes(1, 2147483646, 4) > 0
     assert ccl.ccl_batched_workspace_bytes([(64, 64), (100, 3000)], 8) > 0
+    # volumes: bits + per-brick records + per-brick forest slots; 0 when invalid
+    v1 = ccl.ccl_workspace_bytes3d(16, 16, 32, 6)
+    assert v1 > 0 and v1 % 256 == 0
+    assert ccl.ccl_workspace_bytes3d(17, 16, 32, 6) > v1          # a second brick layer
+    assert ccl.ccl_workspace_bytes3d(16, 16, 32, 4) == 0
+    assert ccl.ccl_workspace_bytes3d(1291, 1291, 1291, 26) == 0   # > 2^31 - 2 voxels
+    assert ccl.ccl_workspace_bytes3d(1 << 27, 1, 1, 6) == 0       # > 2^22 bricks
+    assert ccl.ccl_workspace_bytes3d(1 << 26, 1, 1, 6) > 0
 
 
 @pytest.mark.parametrize("conn", [4, 8])
@@ -112,6 +120,17 @@ def test_host_validation_rejects_before_enqueueing(lib):
     assert lib.ccl_label_regions(None, P(512), 4, 4, 8, addr, 2, None, 0, None) == \
         _lib.CCL_ERR_INVALID_ARG
     assert lib.ccl_label_regions(P(256), P(512), 4, 4, 6, addr, 2, None, 0, None) == \
+        _lib.CCL_ERR_INVALID_ARG
+    # volumes: connectivity 6, 18, 26 only; at most 2^31 - 2 voxels and 2^22 bricks
+    assert lib.ccl_label3d(None, P(512), 2, 2, 2, 6, None, 0, None) == _lib.CCL_ERR_INVALID_ARG
+    assert lib.ccl_label3d(P(256), P(512), 2, 2, 2, 8, None, 0, None) == _lib.CCL_ERR_INVALID_ARG
+    assert lib.ccl_label3d(P(256), P(512), 0, 2, 2, 6, None, 0, None) == _lib.CCL_ERR_INVALID_ARG
+    assert lib.ccl_label3d(P(256), P(512), 2048, 1024, 1024, 26, None, 0, None) == \
+        _lib.CCL_ERR_INVALID_ARG
+    need3 = ccl.ccl_workspace_bytes3d(20, 20, 40, 26)
+    assert lib.ccl_label3d(P(256), P(512), 20, 20, 40, 26, P(4096), need3 - 1, None) == \
+        _lib.CCL_ERR_INVALID_ARG
+    assert lib.ccl_label3d(P(256), P(512), 20, 20, 40, 26, P(4096 + 64), need3, None) == \
         _lib.CCL_ERR_INVALID_ARG
     arr = (_lib.ccl_image * 1)()
     assert lib.ccl_label_batched(arr, 1, 8, None, 0, None) == _lib.CCL_ERR_INVALID_ARG
