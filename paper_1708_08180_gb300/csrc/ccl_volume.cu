@@ -4,9 +4,9 @@
 //   * local merge (Kernel 1, §II-A): a block labels one brick of 32 x 16 x 16
 //     voxels in shared memory; thread t owns one 32-voxel row (a bit word) and
 //     the union-find nodes are the runs of ones in the rows;
-//   * boundary analysis (Kernel 2, §II-B): one thread per (row, word) of the
-//     volume unions the runs that touch across a brick face, in a global
-//     forest over the bricks' border roots;
+//   * boundary analysis (Kernel 2, §II-B): threads over the rows that meet a
+//     brick face union the runs that touch across it, in a global forest over
+//     the bricks' border roots (one kernel for the x faces, one for y and z);
 //   * link (§II-C): a block per brick resolves its border roots and writes the
 //     final labels, four voxels per 16-byte store, a warp covering four rows.
 // The result is the canonical labelling: 0 for background, 1 + the smallest
@@ -151,8 +151,11 @@ __device__ __forceinline__ void touching_runs(uint32_t a, uint32_t b, int dil, F
 }
 
 // Shared-memory union of run nodes; node order is key order (row-major inside
-// the brick), so the larger index is linked under the smaller and every root
-// is its set's smallest voxel.
+// the brick), so the larger root is linked under the smaller and every root is
+// its set's smallest voxel.  The link is an atomic minimum on the larger
+// root's parent: if that node was linked elsewhere meanwhile, the minimum
+// still only lowers its parent, and the union goes on with the parent it had
+// (no retry storm when many threads join the same set at once).
 __device__ __forceinline__ void union_nodes(pnode *P, int a, int b, int &budget, int *err) {
     volatile pnode *vP = P;
     for (;;) {
@@ -161,7 +164,9 @@ __device__ __forceinline__ void union_nodes(pnode *P, int a, int b, int &budget,
         if (a == b) return;
         if (budget < 0) { atomicOr(err, kErrSmemUnion); return; }
         if (a > b) { const int t = a; a = b; b = t; }
-        if (atomicCAS(&P[b], (pnode)b, (pnode)a) == (pnode)b) return;
+        const int old = atomicMin(&P[b], (pnode)a);
+        if (old == b) return;
+        b = old;
     }
 }
 
@@ -291,72 +296,142 @@ __global__ void __launch_bounds__(kThreads) kv_merge(VolArgs a, int *err) {
     }
 }
 
-// Global node of the j-th run of row (y, z) in word w (a border root's run).
-__device__ __forceinline__ bool run_node(const VolArgs &a, int w, int y, int z, int j, gnode &out,
-                                         int *err) {
+// The brick and border slot of the j-th run of row (y, z) in word w (a run on
+// a brick face, so its root holds a slot).
+__device__ __forceinline__ bool run_slot(const VolArgs &a, int w, int y, int z, int j,
+                                         long long &brick, int &slot, int *err) {
     const Geom3 &g = a.g;
-    const long long brick = ((long long)(z / kBZ) * g.nby + y / kBY) * g.nwg + w;
+    brick = ((long long)(z / kBZ) * g.nby + y / kBY) * g.nwg + w;
     const int t = (z % kBZ) * kBY + (y % kBY);
     const int *bw = a.bws + (size_t)brick * kBrickInts;
     const int n = __ldcg(reinterpret_cast<const uint16_t *>(bw + kOffBase) + t) + j;
     const int v = n < kNodes ? __ldcg(bw + kOffLab + n) : 0;
     if (v >= 0 || -v - 1 >= kSlots) { atomicOr(err, kErrResolve); return false; }
-    const int slot = -v - 1;
-    out = node3(__ldcg(bw + kOffKey + slot), brick, slot);
+    slot = -v - 1;
     return true;
 }
 
+__device__ __forceinline__ gnode slot_node(const VolArgs &a, long long brick, int slot) {
+    return node3(__ldcg(a.bws + (size_t)brick * kBrickInts + kOffKey + slot), brick, slot);
+}
+
 // ---------------------------------------------------------------------------
-// Kernel 2: unions across brick faces.  Item i = (row, word); it handles the
-// pairs whose later voxel (in raster order of rows, x last) lies in this word:
-//   x faces: voxel 32w and its neighbours at x = 32w - 1 (all in brick w - 1);
-//   y / z faces: the row pairs of the neighbourhood whose earlier row lies in
-//   another brick (rows on a brick's first y or z layer, or its last y layer
-//   for the (z-1, y+1) pair).
+// Kernel 2a: unions across x faces.  Item i = (row, word w >= 1): voxel 32w of
+// the row and its neighbours at x = 32w - 1 (the last run of a row of brick
+// w - 1).  Neighbour runs of one border root are unioned once.
 template <int CONN>
-__global__ void __launch_bounds__(256) kv_faces(VolArgs a, long long items, int *err) {
+__global__ void __launch_bounds__(256) kv_xfaces(VolArgs a, long long items, int *err) {
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (i >= items) return;
+    const Geom3 &g = a.g;
+    const int nw1 = g.nwg - 1;
+    const int w = 1 + (int)(i % nw1);
+    const long long row = i / nw1;
+    const uint32_t m = __ldcg(a.bits + row * g.nwg + w);
+    if (!(m & 1u)) return;
+    const int y = (int)(row % g.H), z = (int)(row / g.H);
+    const Forest3 F{a.par};
+    int budget = kGlobHopBudget;
+    gnode self = kNoNode;
+    long long last_brick = -1;
+    int last_slot = -1;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy) {
+            if (!x_pair<CONN>(dy, dz)) continue;
+            const int y2 = y + dy, z2 = z + dz;
+            if (y2 < 0 || y2 >= g.H || z2 < 0 || z2 >= g.D) continue;
+            const uint32_t b = __ldcg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + (w - 1));
+            if (!(b >> 31)) continue;
+            long long ob;
+            int os;
+            if (!run_slot(a, w - 1, y2, z2, __popc(b & ~(b << 1)) - 1, ob, os, err)) return;
+            if (ob == last_brick && os == last_slot) continue;
+            last_brick = ob;
+            last_slot = os;
+            if (self == kNoNode) {
+                long long sb;
+                int ss;
+                if (!run_slot(a, w, y, z, 0, sb, ss, err)) return;
+                self = slot_node(a, sb, ss);
+            }
+            gunion(F, self, slot_node(a, ob, os), budget, err);
+        }
+}
+
+// Rows that may pair with a row of another brick along y or z: y % kBY in
+// {0, kBY - 1}, or z a multiple of kBZ (z > 0).  Face row f in raster order of
+// (z, y) -> (z, y).
+__host__ __device__ __forceinline__ int face_ys(int H) {
+    return (H + kBY - 1) / kBY + H / kBY;
+}
+__host__ __device__ __forceinline__ long long face_rows(int D, int H) {
+    const long long full = (D - 1) / kBZ;   // slices z = kBZ, 2 kBZ, ... below D
+    return full * H + (D - full) * face_ys(H);
+}
+__device__ __forceinline__ void face_row(long long f, int H, int &z, int &y) {
+    const int ny = face_ys(H);
+    int yi;
+    if (f < (long long)kBZ * ny) {
+        z = (int)(f / ny);
+        yi = (int)(f % ny);
+    } else {
+        const long long f2 = f - (long long)kBZ * ny;
+        const long long per = (long long)H + (kBZ - 1) * (long long)ny;
+        const long long grp = 1 + f2 / per;
+        long long r = f2 % per;
+        if (r < H) {
+            z = (int)(kBZ * grp);
+            y = (int)r;
+            return;
+        }
+        r -= H;
+        z = (int)(kBZ * grp + 1 + r / ny);
+        yi = (int)(r % ny);
+    }
+    y = kBY * (yi / 2) + ((yi & 1) ? kBY - 1 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 2b: unions across y and z faces.  Item = (face row, row pair k, word):
+// the touching runs of the row and of its k-th earlier neighbour row, when that
+// row lies in another brick.  Consecutive pairs of the same two border roots
+// are unioned once.
+template <int CONN>
+__global__ void __launch_bounds__(256) kv_yzfaces(VolArgs a, long long items, int *err) {
     const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
     if (i >= items) return;
     const Geom3 &g = a.g;
     const int w = (int)(i % g.nwg);
-    const long long row = i / g.nwg;
-    const int y = (int)(row % g.H), z = (int)(row / g.H);
-    const uint32_t m = __ldcg(a.bits + i);
+    const long long fk = i / g.nwg;
+    const int k = (int)(fk % RowPairs<CONN>::n);
+    int y, z;
+    face_row(fk / RowPairs<CONN>::n, g.H, z, y);
+    int dz, dy;
+    const int dil = RowPairs<CONN>::at(k, dz, dy);
+    const int y2 = y + dy, z2 = z + dz;
+    if (y2 < 0 || y2 >= g.H || z2 < 0) return;
+    if (y2 / kBY == y / kBY && z2 / kBZ == z / kBZ) return;   // same brick: merged locally
+    const uint32_t m = __ldcg(a.bits + ((size_t)z * g.H + y) * g.nwg + w);
     if (!m) return;
+    const uint32_t b = __ldcg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + w);
+    if (!b) return;
     const Forest3 F{a.par};
     int budget = kGlobHopBudget;
-    if (w > 0 && (m & 1u)) {
-        gnode self = kNoNode;
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy) {
-                if (!x_pair<CONN>(dy, dz)) continue;
-                const int y2 = y + dy, z2 = z + dz;
-                if (y2 < 0 || y2 >= g.H || z2 < 0 || z2 >= g.D) continue;
-                const uint32_t b = __ldcg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + (w - 1));
-                if (!(b >> 31)) continue;
-                gnode other;
-                if (self == kNoNode && !run_node(a, w, y, z, 0, self, err)) return;
-                if (!run_node(a, w - 1, y2, z2, __popc(b & ~(b << 1)) - 1, other, err)) return;
-                gunion(F, self, other, budget, err);
-            }
-    }
-    const int ly = y % kBY, lz = z % kBZ;
-    if (!(ly == 0 || ly == kBY - 1 || lz == 0)) return;
-#pragma unroll
-    for (int k = 0; k < RowPairs<CONN>::n; ++k) {
-        int dz, dy;
-        const int dil = RowPairs<CONN>::at(k, dz, dy);
-        const int y2 = y + dy, z2 = z + dz;
-        if (y2 < 0 || y2 >= g.H || z2 < 0) continue;
-        if (y2 / kBY == y / kBY && z2 / kBZ == z / kBZ) continue;   // same brick: merged locally
-        const uint32_t b = __ldcg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + w);
-        if (!b) continue;
-        touching_runs(m, b, dil, [&](int ia, int jb) {
-            gnode na, nbn;
-            if (run_node(a, w, y, z, ia, na, err) && run_node(a, w, y2, z2, jb, nbn, err))
-                gunion(F, na, nbn, budget, err);
-        });
-    }
+    int last_sa = -1, last_sb = -1;
+    bool bad = false;
+    touching_runs(m, b, dil, [&](int ia, int jb) {
+        long long pa, pb;
+        int sa, sb;
+        if (bad) return;
+        if (!run_slot(a, w, y, z, ia, pa, sa, err) || !run_slot(a, w, y2, z2, jb, pb, sb, err)) {
+            bad = true;
+            return;
+        }
+        if (sa == last_sa && sb == last_sb) return;
+        last_sa = sa;
+        last_sb = sb;
+        gunion(F, slot_node(a, pa, sa), slot_node(a, pb, sb), budget, err);
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -461,8 +536,12 @@ static void launch_volume(const VolArgs &a, int *err, cudaStream_t stream) {
     const Geom3 &g = a.g;
     const unsigned nbricks = (unsigned)g.nbricks;
     kv_merge<CONN><<<nbricks, kThreads, 0, stream>>>(a, err);
-    const long long items = (long long)g.D * g.H * g.nwg;
-    kv_faces<CONN><<<(unsigned)((items + 255) / 256), 256, 0, stream>>>(a, items, err);
+    if (g.nwg > 1) {
+        const long long items = (long long)g.D * g.H * (g.nwg - 1);
+        kv_xfaces<CONN><<<(unsigned)((items + 255) / 256), 256, 0, stream>>>(a, items, err);
+    }
+    const long long yz = face_rows(g.D, g.H) * RowPairs<CONN>::n * g.nwg;
+    kv_yzfaces<CONN><<<(unsigned)((yz + 255) / 256), 256, 0, stream>>>(a, yz, err);
     kv_link<<<nbricks, kThreads, 0, stream>>>(a, err);
 }
 
