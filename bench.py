@@ -496,7 +496,8 @@ def regions_leg(img, out, ws, stream, reps: int = 50):
             "what": "every equal-value region (foreground and background) of the headline image"}
 
 
-def volume_leg(dev, stream, reps: int = 20, side: int = 512, p: float = 0.5):
+def volume_leg(dev, stream, reps: int = 20, side: int = 512, p: float = 0.5,
+               conns=(6, 18, 26)):
     """ccl_label3d on a side^3 Bernoulli(p) volume at 6-, 18- and 26-connectivity:
     device time per call (CUDA events, after warm-up; input 128 MiB and labels
     512 MiB, both larger than L2) and its voxel rate."""
@@ -509,7 +510,7 @@ def volume_leg(dev, stream, reps: int = 20, side: int = 512, p: float = 0.5):
     out = torch.empty((side, side, side), dtype=torch.int32, device=dev)
     res = {"shape": [side, side, side], "density": p,
            "what": "3-D labelling (bricks of 32x16x16 voxels), labels 1 + smallest voxel index"}
-    for conn in (6, 18, 26):
+    for conn in conns:
         ws = torch.empty(ccl.ccl_workspace_bytes3d(side, side, side, conn), dtype=torch.uint8,
                          device=dev)
         for _ in range(3):
@@ -669,7 +670,7 @@ def run_ours(args, rank, world, local):
     if rank == 0 and not args.no_stats:
         line["component_stats"] = stats_leg(outs[0], stream)
     if rank == 0 and not args.no_volume:
-        line["volume"] = volume_leg(dev, stream)
+        line["volume"] = volume_leg(dev, stream, side=args.volume_side)
     if rank == 0 and not args.no_regions:
         line["label_regions"] = regions_leg(imgs[1 % ROTATE], outs[1 % ROTATE], wss[1 % ROTATE],
                                             stream)
@@ -698,6 +699,12 @@ def main(argv=None) -> int:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stats", action="store_true", help="skip the component-statistics leg")
     ap.add_argument("--no-volume", action="store_true", help="skip the 3-D volume leg")
+    ap.add_argument("--volume-only", action="store_true",
+                    help="run only the 3-D volume leg (one JSON line), e.g. for profiling")
+    ap.add_argument("--volume-side", type=int, default=512, help="volume side (default 512)")
+    ap.add_argument("--volume-conn", type=int, choices=(6, 18, 26), default=None,
+                    help="one volume connectivity (default: 6, 18 and 26)")
+    ap.add_argument("--volume-reps", type=int, default=20)
     ap.add_argument("--no-regions", action="store_true",
                     help="skip the every-region (levels 0 and 1) leg")
     ap.add_argument("--no-batched", action="store_true",
@@ -722,7 +729,24 @@ def main(argv=None) -> int:
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.volume_only:
+        return run_volume_only(args, local)
     return run_ours(args, rank, world, local)
+
+
+def run_volume_only(args, local) -> int:
+    import torch
+
+    import paper_1708_08180_gb300 as ccl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ccl.load()
+    conns = (args.volume_conn,) if args.volume_conn else (6, 18, 26)
+    res = volume_leg(dev, torch.cuda.current_stream(dev), reps=args.volume_reps,
+                     side=args.volume_side, p=args.density, conns=conns)
+    print(json.dumps({"volume": res}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

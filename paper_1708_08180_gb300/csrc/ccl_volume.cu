@@ -253,7 +253,8 @@ __global__ void __launch_bounds__(kThreads) kv_merge(VolArgs a, int *err) {
                                 ((run_at(bits, p) >> 31) && bx + 1 < g.nwg);
             if (border) {
                 const int r = sm.P[n];
-                atomicOr(&sm.flag[r >> 5], 1u << (r & 31));
+                const uint32_t bit = 1u << (r & 31);
+                if (!(sm.flag[r >> 5] & bit)) atomicOr(&sm.flag[r >> 5], bit);
             }
         }
     }
