@@ -1,12 +1,19 @@
 // ccl_volume.cu -- labelling of 3-D volumes (the "2D/3D grid" of §I) with the
 // paper's three phases one dimension up: tiles become bricks, tile seams become
 // brick faces.
-//   * local merge (Kernel 1, §II-A): a block labels one brick of 32 x 16 x 16
-//     voxels in shared memory; thread t owns one 32-voxel row (a bit word) and
-//     the union-find nodes are the runs of ones in the rows;
-//   * boundary analysis (Kernel 2, §II-B): threads over the rows that meet a
-//     brick face union the runs that touch across it, in a global forest over
-//     the bricks' border roots (one kernel for the x faces, one for y and z);
+//   * A strip is SY x SZ neighbouring rows (one row at 6-connectivity, two rows
+//     along y at 18, 2 x 2 rows at 26), read as one 32-voxel word per row.
+//     Every run of ones of the OR of a strip's rows is connected (its voxels at
+//     x and x + 1 are neighbours whatever their rows), so the runs of the OR,
+//     "segments", are the union-find nodes.  A brick is one word along x by
+//     16 x 16 strips; thread t of a block owns strip (t % 16, t / 16).
+//   * local merge (Kernel 1, §II-A): a block joins the segments of its brick in
+//     shared memory, each strip with its earlier neighbour strips through the
+//     rows that face each other;
+//   * boundary analysis (Kernel 2, §II-B): threads over the rows and strips that
+//     meet a brick face union the segments that touch across it, in a global
+//     forest over the bricks' border roots (one kernel for the x faces, one for
+//     y and z);
 //   * link (§II-C): a block per brick resolves its border roots and writes the
 //     final labels, four voxels per 16-byte store, a warp covering four rows.
 // The result is the canonical labelling: 0 for background, 1 + the smallest
@@ -17,57 +24,76 @@
 namespace ccl {
 namespace vol {
 
-// Brick = one 32-voxel word along x, kBY rows along y, kBZ slices along z;
-// thread t of a block owns row (ly, lz) = (t % kBY, t / kBY).
-constexpr int kBY = 16, kBZ = 16;
-static_assert(kBY * kBZ == kThreads, "one thread per brick row");
-constexpr int kNodes = kThreads * 16;   // at most 16 runs in a 32-voxel word
-// Border roots per brick: every one owns a run on a y or z face (60 rows of at
-// most 16 runs) or a run touching an x face (196 inner rows, at most 2 runs
-// each): at most 1352.
+constexpr int kStrips = 16;   // strips per brick along y and along z
+static_assert(kStrips * kStrips == kThreads, "one thread per strip");
+constexpr int kNodes = kThreads * 16;   // at most 16 segments in a 32-voxel word
+constexpr int kNodeBits = 12;           // node index inside a brick
+constexpr int kNodeMask = (1 << kNodeBits) - 1;
+static_assert(kNodes == 1 << kNodeBits, "node index width");
+// Border roots per brick: every one owns a segment of a strip on a y or z face
+// (60 strips of at most 16 segments) or a segment touching an x face (196
+// inner strips, at most 2 each): at most 1352.
 constexpr int kSlots = 2048;
 constexpr int kSlotBits = 11;
 constexpr int kBrickBits = 22;          // global node id: key << 33 | brick << 11 | slot
 constexpr long long kMaxBricks = 1ll << kBrickBits;
 static_assert(kSlotBits + kBrickBits == 33, "31-bit key in the top bits of a node id");
 // Per-brick workspace, in ints from the brick's base:
-//   [0] border roots, [1] run nodes;
-//   [kOffBase, kOffLab)  rank of each row's first run node (uint16 per row);
-//   [kOffLab, kOffKey)   label of each run node: 1 + the voxel index of its
-//                        root's first voxel, or -(slot + 1) for a border root;
+//   [0] border roots, [1] segments;
+//   [kOffBase, kOffSt)   rank of each strip's first segment (uint16 per strip);
+//   [kOffSt, kOffLab)    segment starts of each strip (the runs of its OR);
+//   [kOffLab, kOffKey)   label of each segment: 1 + the voxel index of its
+//                        root's smallest voxel, or -(slot + 1) for a border root;
 //   [kOffKey, ...)       key (smallest voxel index) of each border root.
 constexpr int kOffBase = 4;
-constexpr int kOffLab = kOffBase + kThreads / 2;   // 16-byte aligned
+constexpr int kOffSt = kOffBase + kThreads / 2;
+constexpr int kOffLab = kOffSt + kThreads;
 constexpr int kOffKey = kOffLab + kNodes;
 constexpr int kBrickInts = (kOffKey + kSlots + 63) & ~63;   // 256-byte multiple
-static_assert(kOffLab % 4 == 0, "16-byte aligned node labels");
+static_assert(kOffLab % 4 == 0, "16-byte aligned segment labels");
+
+// Strip shape: every pair of voxels of the strip's rows whose x differ by at
+// most one is a neighbour pair (|dy| + |dz| <= 1 at 18, any at 26).
+template <int CONN> struct Strip {
+    static constexpr int SY = CONN == 6 ? 1 : 2;
+    static constexpr int SZ = CONN == 26 ? 2 : 1;
+    static constexpr int R = SY * SZ;   // row rr = k * SY + j: j along y, k along z
+};
+inline int strip_sy(int conn) { return conn == 6 ? 1 : 2; }
+inline int strip_sz(int conn) { return conn == 26 ? 2 : 1; }
 
 struct Geom3 {
     int D, H, W;
+    int sy, sz;     // strip rows along y and z
     int nwg;        // 32-voxel words per row = bricks along x
+    int nsy, nsz;   // strips along y and z
     int nby, nbz;   // bricks along y and z
     long long nbricks;
 };
 
-inline Geom3 make_geom3(int D, int H, int W) {
+inline Geom3 make_geom3(int D, int H, int W, int conn) {
     Geom3 g;
     g.D = D;
     g.H = H;
     g.W = W;
+    g.sy = strip_sy(conn);
+    g.sz = strip_sz(conn);
     g.nwg = (int)(((long long)W + 31) / 32);
-    g.nby = (H + kBY - 1) / kBY;
-    g.nbz = (D + kBZ - 1) / kBZ;
+    g.nsy = (H + g.sy - 1) / g.sy;
+    g.nsz = (D + g.sz - 1) / g.sz;
+    g.nby = (g.nsy + kStrips - 1) / kStrips;
+    g.nbz = (g.nsz + kStrips - 1) / kStrips;
     g.nbricks = (long long)g.nwg * g.nby * g.nbz;
     return g;
 }
 
-inline bool dims_ok(int D, int H, int W) {
+inline bool valid_conn3(int c) { return c == 6 || c == 18 || c == 26; }
+
+inline bool dims_ok(int D, int H, int W, int conn) {
     if (D < 1 || H < 1 || W < 1) return false;
     if ((long long)D * H > 2147483646LL / W) return false;   // 1 + index fits int32
-    return make_geom3(D, H, W).nbricks <= kMaxBricks;
+    return make_geom3(D, H, W, conn).nbricks <= kMaxBricks;
 }
-
-inline bool valid_conn3(int c) { return c == 6 || c == 18 || c == 26; }
 
 inline size_t bits_bytes3(const Geom3 &g) {
     return ((size_t)g.D * g.H * g.nwg * 4u + 255u) & ~(size_t)255u;
@@ -98,19 +124,37 @@ __device__ __forceinline__ gnode node3(int key, long long brick, int slot) {
            (gnode)slot;
 }
 
-// Row pairs inside the neighbourhood: the k-th offset (dz, dy) from a row to an
-// earlier row, and whether voxels of the two rows may differ by one in x.
-//   6:  (0,-1) (-1,0), same x only
-//   18: (0,-1) (-1,0) with x +-1; (-1,-1) (-1,+1) same x only
-//   26: all four with x +-1
-template <int CONN> struct RowPairs {
-    static constexpr int n = CONN == 6 ? 2 : 4;
-    __device__ static __forceinline__ int at(int k, int &dz, int &dy) {
-        dz = k == 0 ? 0 : -1;
-        dy = k == 0 ? -1 : k == 1 ? 0 : k == 2 ? -1 : 1;
-        return CONN == 26 ? 1 : CONN == 18 ? (k < 2 ? 1 : 0) : 0;
-    }
+// Pairs of neighbouring strips, the other strip earlier in the brick: offset
+// (dz, dy) in strips, the rows of each strip that face the other (bit rr of a
+// mask = row rr), and the x reach dil: a voxel of one row set and a voxel of
+// the other are neighbours exactly when their x differ by at most dil.
+struct StripPair {
+    int dz, dy, ma, mb, dil;
 };
+
+template <int CONN> __host__ __device__ constexpr int n_pairs() {
+    return CONN == 6 ? 2 : CONN == 18 ? 6 : 4;
+}
+
+template <int CONN> __device__ __forceinline__ StripPair strip_pair(int k) {
+    if (CONN == 6) return k == 0 ? StripPair{0, -1, 1, 1, 0} : StripPair{-1, 0, 1, 1, 0};
+    if (CONN == 18) {   // rows: 0 = even y, 1 = odd y
+        switch (k) {
+            case 0: return {0, -1, 1, 2, 1};    // strip below in y: facing rows, x +- 1
+            case 1: return {-1, 0, 3, 3, 0};    // strip below in z, same x: any rows
+            case 2: return {-1, 0, 1, 1, 1};    // strip below in z, same y: x +- 1
+            case 3: return {-1, 0, 2, 2, 1};
+            case 4: return {-1, -1, 1, 2, 0};   // diagonal strips: facing rows, same x
+            default: return {-1, 1, 2, 1, 0};
+        }
+    }
+    switch (k) {        // 26, rows rr = zz * 2 + yy
+        case 0: return {0, -1, 1 | 4, 2 | 8, 1};
+        case 1: return {-1, 0, 1 | 2, 4 | 8, 1};
+        case 2: return {-1, -1, 1, 8, 1};
+        default: return {-1, 1, 2, 4, 1};
+    }
+}
 
 // Whether the voxel at (x - 1, y + dy, z + dz) is a neighbour of (x, y, z).
 template <int CONN> __device__ __forceinline__ bool x_pair(int dy, int dz) {
@@ -125,56 +169,84 @@ __device__ __forceinline__ uint32_t run_at(uint32_t a, int p) {
     return (len >= 32 ? 0xFFFFFFFFu : ((1u << len) - 1u)) << p;
 }
 
-// Touching run pairs of two rows a and b (words at the same x): voxels x and
-// x' touch when |x - x'| <= dil.  Each run of a is paired with the run of b
-// holding the lowest b-voxel it touches, and each run of b with the run of a
-// holding the lowest a-voxel it touches.  These pairs connect all mutually
-// touching runs: if neither rule picks a touching pair (A, B), then A's pick
-// B' lies left of B and B's pick A' left of A, A' touches B' (the intervals
-// interleave), and induction on the position links A' with B'.
-// f(i, j): the i-th run of a and the j-th run of b.
+// Touching runs of two bit words a and b: voxels x and x' touch when
+// |x - x'| <= dil.  f(p, q) gets a bit p of a run of a and a bit q of a run of
+// b for a set of touching run pairs that connects all of them:
+//   dil = 0: two runs touch iff they overlap, and their overlap is one run of
+//   a & b; so the runs of a & b list every touching pair exactly once.
+//   dil = 1: each run of a is paired with the run of b holding the lowest
+//   b-voxel it touches, and each run of b with the run of a holding the lowest
+//   a-voxel it touches.  If neither rule picks a touching pair (A, B), A's pick
+//   B' lies left of B and B's pick A' left of A, A' touches B' (the intervals
+//   interleave), and induction on the position links A' with B'.
 template <class F>
-__device__ __forceinline__ void touching_runs(uint32_t a, uint32_t b, int dil, F &&f) {
-    const uint32_t sa = a & ~(a << 1), sb = b & ~(b << 1);
-    int i = 0;
-    for (uint32_t s = sa; s; s &= s - 1, ++i) {
-        const uint32_t run = run_at(a, __ffs(s) - 1);
-        const uint32_t hit = b & (dil ? (run | (run << 1) | (run >> 1)) : run);
-        if (hit) f(i, __popc(sb & le_mask(__ffs(hit) - 1)) - 1);
+__device__ __forceinline__ void touching_bits(uint32_t a, uint32_t b, int dil, F &&f) {
+    if (!dil) {
+        const uint32_t o = a & b;
+        for (uint32_t s = o & ~(o << 1); s; s &= s - 1) {
+            const int p = __ffs(s) - 1;
+            f(p, p);
+        }
+        return;
     }
-    int j = 0;
-    for (uint32_t s = sb; s; s &= s - 1, ++j) {
-        const uint32_t run = run_at(b, __ffs(s) - 1);
-        const uint32_t hit = a & (dil ? (run | (run << 1) | (run >> 1)) : run);
-        if (hit) f(__popc(sa & le_mask(__ffs(hit) - 1)) - 1, j);
+    for (uint32_t s = a & ~(a << 1); s; s &= s - 1) {
+        const int p = __ffs(s) - 1;
+        const uint32_t run = run_at(a, p);
+        const uint32_t hit = b & (run | (run << 1) | (run >> 1));
+        if (hit) f(p, __ffs(hit) - 1);
+    }
+    for (uint32_t s = b & ~(b << 1); s; s &= s - 1) {
+        const int q = __ffs(s) - 1;
+        const uint32_t run = run_at(b, q);
+        const uint32_t hit = a & (run | (run << 1) | (run >> 1));
+        if (hit) f(__ffs(hit) - 1, q);
     }
 }
 
-// Shared-memory union of run nodes; node order is key order (row-major inside
-// the brick), so the larger root is linked under the smaller and every root is
-// its set's smallest voxel.  The link is an atomic minimum on the larger
-// root's parent: if that node was linked elsewhere meanwhile, the minimum
-// still only lowers its parent, and the union goes on with the parent it had
-// (no retry storm when many threads join the same set at once).
-__device__ __forceinline__ void union_nodes(pnode *P, int a, int b, int &budget, int *err) {
-    volatile pnode *vP = P;
+// Shared-memory union-find over segments.  P[n] = key(parent) << 12 | parent,
+// where key is the brick-local index of a segment's smallest voxel, so the
+// smaller packed value is the smaller key.  A root holds its own packed id;
+// links go from the larger key to the smaller by an atomic minimum, and a node
+// linked elsewhere meanwhile only has its parent lowered: the union goes on
+// with the parent it had (no retry storm when many threads join one set).
+__device__ __forceinline__ int pfind(volatile int *P, int x, int &budget, int *err) {
     for (;;) {
-        a = sfind(vP, a, budget, err);
-        b = sfind(vP, b, budget, err);
+        if (--budget < 0) { atomicOr(err, kErrSmemFind); return x; }
+        const int p = P[x] & kNodeMask;
+        if (p == x) return x;
+        const int gp = P[p];
+        if ((gp & kNodeMask) == p) return p;
+        P[x] = gp;   // path halving: gp is an ancestor of x
+        x = gp & kNodeMask;
+    }
+}
+
+__device__ __forceinline__ void punion(int *P, const uint16_t *K, int a, int b, int &budget,
+                                       int *err) {
+    volatile int *vP = P;
+    for (;;) {
+        a = pfind(vP, a, budget, err);
+        b = pfind(vP, b, budget, err);
         if (a == b) return;
         if (budget < 0) { atomicOr(err, kErrSmemUnion); return; }
-        if (a > b) { const int t = a; a = b; b = t; }
-        const int old = atomicMin(&P[b], (pnode)a);
-        if (old == b) return;
-        b = old;
+        int pa = ((int)K[a] << kNodeBits) | a, pb = ((int)K[b] << kNodeBits) | b;
+        if (pa > pb) {   // link the root with the larger key, b, under a
+            const int tp = pa; pa = pb; pb = tp;
+            b = a;
+        }
+        const int old = atomicMin(&P[b], pa);
+        if (old == pb) return;
+        a = pa & kNodeMask;
+        b = old & kNodeMask;
     }
 }
 
-struct SmemVolMerge {
-    pnode P[kNodes];              // parent of each run node
-    uint16_t K[kNodes];           // brick-local index (t * 32 + x) of the node's first voxel
-    uint32_t bits[kThreads];      // each row's word
-    int base[kThreads];           // rank of each row's first node
+template <int R> struct SmemVolMerge {
+    int P[kNodes];                // packed parent of each segment
+    uint16_t K[kNodes];           // brick-local index of the segment's smallest voxel
+    uint32_t rows[R][kThreads];   // each strip's rows
+    uint32_t st[kThreads];        // segment starts of each strip
+    int base[kThreads];           // rank of each strip's first segment
     uint32_t flag[kNodes / 32];   // roots whose component reaches a brick face
     int fbase[kNodes / 32];       // slot of the first flagged root of each flag word
     int warp_sums[kThreads / 32];
@@ -192,65 +264,112 @@ __device__ __forceinline__ void brick_coords(const Geom3 &g, long long brick, in
 // Kernel 1: local merge of one brick.
 template <int CONN>
 __global__ void __launch_bounds__(kThreads) kv_merge(VolArgs a, int *err) {
-    __shared__ SmemVolMerge sm;
+    constexpr int SY = Strip<CONN>::SY, SZ = Strip<CONN>::SZ, R = Strip<CONN>::R;
+    constexpr int BYR = kStrips * SY;   // rows of a brick along y
+    __shared__ SmemVolMerge<R> sm;
     const Geom3 &g = a.g;
     const int t = threadIdx.x;
     const long long brick = blockIdx.x;
     int bx, by, bz;
     brick_coords(g, brick, bx, by, bz);
-    const int ly = t % kBY, lz = t / kBY;
-    const int x0 = 32 * bx, y = by * kBY + ly, z = bz * kBZ + lz;
-    const bool in = y < g.H && z < g.D;
-    const int row = in ? z * g.H + y : 0;
+    const int sy = t % kStrips, sz = t / kStrips;
+    const int x0 = 32 * bx;
+    const int gsy = by * kStrips + sy, gsz = bz * kStrips + sz;
     const uint8_t *vol_end = a.vol + (size_t)g.D * g.H * g.W;
-    const uint32_t bits = in ? load_row_bits(a.vol, vol_end, row, x0, g.W, a.aligned16 != 0) : 0u;
-    const uint32_t st = bits & ~(bits << 1);
-    sm.bits[t] = bits;
+    uint32_t rows[R];
+    uint32_t seg = 0;
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+        const int y = gsy * SY + rr % SY, z = gsz * SZ + rr / SY;
+        rows[rr] = (y < g.H && z < g.D)
+                       ? load_row_bits(a.vol, vol_end, z * g.H + y, x0, g.W, a.aligned16 != 0)
+                       : 0u;
+        sm.rows[rr][t] = rows[rr];
+        seg |= rows[rr];
+    }
+    const uint32_t st = seg & ~(seg << 1);
+    sm.st[t] = st;
     int total;
-    const int base = block_excl_scan(__popc(st), sm.warp_sums, total);   // syncs: bits visible
+    const int base = block_excl_scan(__popc(st), sm.warp_sums, total);   // syncs
     sm.base[t] = base;
-    {
+    {   // key of each segment: its first voxel in (z, y, x) order
         int n = base;
         for (uint32_t s = st; s; s &= s - 1, ++n) {
-            sm.P[n] = n;
-            sm.K[n] = (uint16_t)(t * 32 + __ffs(s) - 1);
+            const uint32_t m = run_at(seg, __ffs(s) - 1);
+            int key = 0;
+#pragma unroll
+            for (int rr = R - 1; rr >= 0; --rr) {
+                const uint32_t hit = rows[rr] & m;
+                if (hit) {
+                    const int ly = sy * SY + rr % SY, lz = sz * SZ + rr / SY;
+                    key = (lz * BYR + ly) * 32 + __ffs(hit) - 1;
+                }
+            }
+            sm.K[n] = (uint16_t)key;
+            sm.P[n] = (key << kNodeBits) | n;
         }
     }
     for (int k = t; k < kNodes / 32; k += kThreads) sm.flag[k] = 0u;
     __syncthreads();
 
-    // unions with the earlier rows of the brick
+    // unions with the earlier neighbour strips of the brick
     int budget = kSmemHopBudget;
-    if (bits) {
+    if (seg) {
 #pragma unroll
-        for (int k = 0; k < RowPairs<CONN>::n; ++k) {
-            int dz, dy;
-            const int dil = RowPairs<CONN>::at(k, dz, dy);
-            const int lz2 = lz + dz, ly2 = ly + dy;
-            if (lz2 < 0 || ly2 < 0 || ly2 >= kBY) continue;
-            const int t2 = lz2 * kBY + ly2;
-            const uint32_t b = sm.bits[t2];
-            if (!b) continue;
+        for (int k = 0; k < n_pairs<CONN>(); ++k) {
+            const StripPair sp = strip_pair<CONN>(k);
+            const int sy2 = sy + sp.dy, sz2 = sz + sp.dz;
+            if (sz2 < 0 || sy2 < 0 || sy2 >= kStrips) continue;
+            const int t2 = sz2 * kStrips + sy2;
+            uint32_t fa = 0, fb = 0;
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr) {
+                if ((sp.ma >> rr) & 1) fa |= rows[rr];
+                if ((sp.mb >> rr) & 1) fb |= sm.rows[rr][t2];
+            }
+            if (!fa || !fb) continue;
+            const uint32_t st2 = sm.st[t2];
             const int base2 = sm.base[t2];
-            touching_runs(bits, b, dil, [&](int i, int j) {
-                union_nodes(sm.P, base + i, base2 + j, budget, err);
+            touching_bits(fa, fb, sp.dil, [&](int p, int q) {
+                punion(sm.P, sm.K, base + __popc(st & le_mask(p)) - 1,
+                       base2 + __popc(st2 & le_mask(q)) - 1, budget, err);
             });
         }
     }
     __syncthreads();
-    // every node points at its root
-    for (int n = t; n < total; n += kThreads) sm.P[n] = sfind(sm.P, n, budget, err);
+    // every segment points at its root: read-only walks first (the forest no
+    // longer changes), then, after a barrier, the stores, so that no walk sees
+    // a half-rewritten parent
+    constexpr int kPer = kNodes / kThreads;
+    int roots[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        int r = t + i * kThreads;
+        if (r < total) {
+            for (;;) {
+                if (--budget < 0) { atomicOr(err, kErrSmemFind); break; }
+                const int p = sm.P[r] & kNodeMask;
+                if (p == r) break;
+                r = p;
+            }
+        }
+        roots[i] = r;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kPer; ++i)
+        if (t + i * kThreads < total) sm.P[t + i * kThreads] = roots[i];   // plain index
     __syncthreads();
 
-    // roots of runs on a face shared with another brick
-    const bool yzface = (ly == 0 && by > 0) || (ly == kBY - 1 && by + 1 < g.nby) ||
-                        (lz == 0 && bz > 0) || (lz == kBZ - 1 && bz + 1 < g.nbz);
+    // roots of segments on a face shared with another brick
+    const bool yzface = (sy == 0 && by > 0) || (sy == kStrips - 1 && by + 1 < g.nby) ||
+                        (sz == 0 && bz > 0) || (sz == kStrips - 1 && bz + 1 < g.nbz);
     {
         int n = base;
         for (uint32_t s = st; s; s &= s - 1, ++n) {
             const int p = __ffs(s) - 1;
             const bool border = yzface || (p == 0 && bx > 0) ||
-                                ((run_at(bits, p) >> 31) && bx + 1 < g.nwg);
+                                ((run_at(seg, p) >> 31) && bx + 1 < g.nwg);
             if (border) {
                 const int r = sm.P[n];
                 const uint32_t bit = 1u << (r & 31);
@@ -273,15 +392,21 @@ __global__ void __launch_bounds__(kThreads) kv_merge(VolArgs a, int *err) {
         bw[1] = total;
         if (nb > kSlots) atomicOr(err, kErrBorderCap);
     }
-    if (in) a.bits[(size_t)row * g.nwg + bx] = bits;
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+        const int y = gsy * SY + rr % SY, z = gsz * SZ + rr / SY;
+        if (y < g.H && z < g.D) a.bits[((size_t)z * g.H + y) * g.nwg + bx] = rows[rr];
+    }
     reinterpret_cast<uint16_t *>(bw + kOffBase)[t] = (uint16_t)base;
+    bw[kOffSt + t] = (int)st;
     const long long HW = (long long)g.H * g.W;
     for (int n = t; n < total; n += kThreads) {
         const int r = sm.P[n];
         const uint32_t fw = sm.flag[r >> 5];
         const int k = sm.K[r];
-        const int key = (int)((long long)(bz * kBZ + (k >> 9)) * HW +
-                              (long long)(by * kBY + ((k >> 5) & (kBY - 1))) * g.W + x0 + (k & 31));
+        const int lz = k / (32 * BYR), ly = (k / 32) % BYR;
+        const int key = (int)((long long)(bz * kStrips * SZ + lz) * HW +
+                              (long long)(by * BYR + ly) * g.W + x0 + (k & 31));
         int v;
         if ((fw >> (r & 31)) & 1u) {
             const int slot = sm.fbase[r >> 5] + __popc(fw & ((1u << (r & 31)) - 1u));
@@ -297,16 +422,18 @@ __global__ void __launch_bounds__(kThreads) kv_merge(VolArgs a, int *err) {
     }
 }
 
-// The brick and border slot of the j-th run of row (y, z) in word w (a run on
-// a brick face, so its root holds a slot).
-__device__ __forceinline__ bool run_slot(const VolArgs &a, int w, int y, int z, int j,
+// The brick and border slot of the segment holding bit `bit` of word w in
+// strip (gsy, gsz) (a segment on a brick face, so its root holds a slot).
+__device__ __forceinline__ bool seg_slot(const VolArgs &a, int w, int gsy, int gsz, int bit,
                                          long long &brick, int &slot, int *err) {
     const Geom3 &g = a.g;
-    brick = ((long long)(z / kBZ) * g.nby + y / kBY) * g.nwg + w;
-    const int t = (z % kBZ) * kBY + (y % kBY);
+    brick = ((long long)(gsz / kStrips) * g.nby + gsy / kStrips) * g.nwg + w;
+    const int t = (gsz % kStrips) * kStrips + (gsy % kStrips);
     const int *bw = a.bws + (size_t)brick * kBrickInts;
-    const int n = __ldcg(reinterpret_cast<const uint16_t *>(bw + kOffBase) + t) + j;
-    const int v = n < kNodes ? __ldcg(bw + kOffLab + n) : 0;
+    const int base = __ldcg(reinterpret_cast<const uint16_t *>(bw + kOffBase) + t);
+    const uint32_t st = (uint32_t)__ldcg(bw + kOffSt + t);
+    const int n = base + __popc(st & le_mask(bit)) - 1;
+    const int v = (n >= 0 && n < kNodes) ? __ldcg(bw + kOffLab + n) : 0;
     if (v >= 0 || -v - 1 >= kSlots) { atomicOr(err, kErrResolve); return false; }
     slot = -v - 1;
     return true;
@@ -317,137 +444,154 @@ __device__ __forceinline__ gnode slot_node(const VolArgs &a, long long brick, in
 }
 
 // ---------------------------------------------------------------------------
-// Kernel 2a: unions across x faces.  Item i = (row, word w >= 1): voxel 32w of
-// the row and its neighbours at x = 32w - 1 (the last run of a row of brick
-// w - 1).  Neighbour runs of one border root are unioned once.
+// Kernel 2a: unions across x faces.  Item i = (strip, word w >= 1): the
+// segment at voxel 32w of the strip and the segments at x = 32w - 1 (in brick
+// w - 1) of every neighbour of a voxel 32w of the strip's rows.  Consecutive
+// neighbours of one border root are unioned once.
 template <int CONN>
 __global__ void __launch_bounds__(256) kv_xfaces(VolArgs a, long long items, int *err) {
+    constexpr int SY = Strip<CONN>::SY, SZ = Strip<CONN>::SZ, R = Strip<CONN>::R;
     const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
     if (i >= items) return;
     const Geom3 &g = a.g;
     const int nw1 = g.nwg - 1;
     const int w = 1 + (int)(i % nw1);
-    const long long row = i / nw1;
-    const uint32_t m = __ldcg(a.bits + row * g.nwg + w);
-    if (!(m & 1u)) return;
-    const int y = (int)(row % g.H), z = (int)(row / g.H);
+    const long long sidx = i / nw1;
+    const int gsy = (int)(sidx % g.nsy), gsz = (int)(sidx / g.nsy);
     const Forest3 F{a.par};
     int budget = kGlobHopBudget;
     gnode self = kNoNode;
     long long last_brick = -1;
     int last_slot = -1;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy) {
-            if (!x_pair<CONN>(dy, dz)) continue;
-            const int y2 = y + dy, z2 = z + dz;
-            if (y2 < 0 || y2 >= g.H || z2 < 0 || z2 >= g.D) continue;
-            const uint32_t b = __ldcg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + (w - 1));
-            if (!(b >> 31)) continue;
-            long long ob;
-            int os;
-            if (!run_slot(a, w - 1, y2, z2, __popc(b & ~(b << 1)) - 1, ob, os, err)) return;
-            if (ob == last_brick && os == last_slot) continue;
-            last_brick = ob;
-            last_slot = os;
-            if (self == kNoNode) {
-                long long sb;
-                int ss;
-                if (!run_slot(a, w, y, z, 0, sb, ss, err)) return;
-                self = slot_node(a, sb, ss);
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+        const int y = gsy * SY + rr % SY, z = gsz * SZ + rr / SY;
+        if (y >= g.H || z >= g.D) continue;
+        if (!(__ldcg(a.bits + ((size_t)z * g.H + y) * g.nwg + w) & 1u)) continue;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy) {
+                if (!x_pair<CONN>(dy, dz)) continue;
+                const int y2 = y + dy, z2 = z + dz;
+                if (y2 < 0 || y2 >= g.H || z2 < 0 || z2 >= g.D) continue;
+                const uint32_t b = __ldcg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + (w - 1));
+                if (!(b >> 31)) continue;
+                long long ob;
+                int os;
+                if (!seg_slot(a, w - 1, y2 / SY, z2 / SZ, 31, ob, os, err)) return;
+                if (ob == last_brick && os == last_slot) continue;
+                last_brick = ob;
+                last_slot = os;
+                if (self == kNoNode) {
+                    long long sb;
+                    int ss;
+                    if (!seg_slot(a, w, gsy, gsz, 0, sb, ss, err)) return;
+                    self = slot_node(a, sb, ss);
+                }
+                gunion(F, self, slot_node(a, ob, os), budget, err);
             }
-            gunion(F, self, slot_node(a, ob, os), budget, err);
-        }
+    }
 }
 
-// Rows that may pair with a row of another brick along y or z: y % kBY in
-// {0, kBY - 1}, or z a multiple of kBZ (z > 0).  Face row f in raster order of
-// (z, y) -> (z, y).
-__host__ __device__ __forceinline__ int face_ys(int H) {
-    return (H + kBY - 1) / kBY + H / kBY;
+// Strips that may pair with a strip of another brick along y or z: strip y
+// index % 16 in {0, 15}, or strip z index a positive multiple of 16.  Face
+// strip f in raster order of (strip z, strip y) -> (strip z, strip y), for a
+// grid of nsz x nsy strips.
+__host__ __device__ __forceinline__ int face_ys(int nsy) {
+    return (nsy + kStrips - 1) / kStrips + nsy / kStrips;
 }
-__host__ __device__ __forceinline__ long long face_rows(int D, int H) {
-    const long long full = (D - 1) / kBZ;   // slices z = kBZ, 2 kBZ, ... below D
-    return full * H + (D - full) * face_ys(H);
+__host__ __device__ __forceinline__ long long face_strips(int nsz, int nsy) {
+    const long long full = (nsz - 1) / kStrips;   // z = 16, 32, ... below nsz
+    return full * nsy + (nsz - full) * face_ys(nsy);
 }
-__device__ __forceinline__ void face_row(long long f, int H, int &z, int &y) {
-    const int ny = face_ys(H);
+__device__ __forceinline__ void face_strip(long long f, int nsy, int &z, int &y) {
+    const int ny = face_ys(nsy);
     int yi;
-    if (f < (long long)kBZ * ny) {
+    if (f < (long long)kStrips * ny) {
         z = (int)(f / ny);
         yi = (int)(f % ny);
     } else {
-        const long long f2 = f - (long long)kBZ * ny;
-        const long long per = (long long)H + (kBZ - 1) * (long long)ny;
+        const long long f2 = f - (long long)kStrips * ny;
+        const long long per = (long long)nsy + (kStrips - 1) * (long long)ny;
         const long long grp = 1 + f2 / per;
         long long r = f2 % per;
-        if (r < H) {
-            z = (int)(kBZ * grp);
+        if (r < nsy) {
+            z = (int)(kStrips * grp);
             y = (int)r;
             return;
         }
-        r -= H;
-        z = (int)(kBZ * grp + 1 + r / ny);
+        r -= nsy;
+        z = (int)(kStrips * grp + 1 + r / ny);
         yi = (int)(r % ny);
     }
-    y = kBY * (yi / 2) + ((yi & 1) ? kBY - 1 : 0);
+    y = kStrips * (yi / 2) + ((yi & 1) ? kStrips - 1 : 0);
 }
 
 // ---------------------------------------------------------------------------
-// Kernel 2b: unions across y and z faces.  Item = (face row, row pair k, word):
-// the touching runs of the row and of its k-th earlier neighbour row, when that
-// row lies in another brick.  Consecutive pairs of the same two border roots
-// are unioned once.
+// Kernel 2b: unions across y and z faces.  Item = (face strip, strip pair k,
+// word): the touching segments of the strip and of its k-th earlier neighbour
+// strip, when that strip lies in another brick.  Consecutive pairs of the same
+// two border roots are unioned once.
 template <int CONN>
 __global__ void __launch_bounds__(256) kv_yzfaces(VolArgs a, long long items, int *err) {
+    constexpr int SY = Strip<CONN>::SY, SZ = Strip<CONN>::SZ, R = Strip<CONN>::R;
     const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
     if (i >= items) return;
     const Geom3 &g = a.g;
     const int w = (int)(i % g.nwg);
     const long long fk = i / g.nwg;
-    const int k = (int)(fk % RowPairs<CONN>::n);
-    int y, z;
-    face_row(fk / RowPairs<CONN>::n, g.H, z, y);
-    int dz, dy;
-    const int dil = RowPairs<CONN>::at(k, dz, dy);
-    const int y2 = y + dy, z2 = z + dz;
-    if (y2 < 0 || y2 >= g.H || z2 < 0) return;
-    if (y2 / kBY == y / kBY && z2 / kBZ == z / kBZ) return;   // same brick: merged locally
-    const uint32_t m = __ldcg(a.bits + ((size_t)z * g.H + y) * g.nwg + w);
-    if (!m) return;
-    const uint32_t b = __ldcg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + w);
-    if (!b) return;
+    const StripPair sp = strip_pair<CONN>((int)(fk % n_pairs<CONN>()));
+    int gsy, gsz;
+    face_strip(fk / n_pairs<CONN>(), g.nsy, gsz, gsy);
+    const int gsy2 = gsy + sp.dy, gsz2 = gsz + sp.dz;
+    if (gsy2 < 0 || gsy2 >= g.nsy || gsz2 < 0) return;
+    if (gsy2 / kStrips == gsy / kStrips && gsz2 / kStrips == gsz / kStrips) return;
+    uint32_t fa = 0, fb = 0;
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+        const int y = gsy * SY + rr % SY, z = gsz * SZ + rr / SY;
+        if (((sp.ma >> rr) & 1) && y < g.H && z < g.D)
+            fa |= __ldcg(a.bits + ((size_t)z * g.H + y) * g.nwg + w);
+        const int y2 = gsy2 * SY + rr % SY, z2 = gsz2 * SZ + rr / SY;
+        if (((sp.mb >> rr) & 1) && y2 < g.H && z2 < g.D)
+            fb |= __ldcg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + w);
+    }
+    if (!fa || !fb) return;
     const Forest3 F{a.par};
     int budget = kGlobHopBudget;
     int last_sa = -1, last_sb = -1;
     bool bad = false;
-    touching_runs(m, b, dil, [&](int ia, int jb) {
-        long long pa, pb;
+    touching_bits(fa, fb, sp.dil, [&](int p, int q) {
+        long long ba, bb;
         int sa, sb;
         if (bad) return;
-        if (!run_slot(a, w, y, z, ia, pa, sa, err) || !run_slot(a, w, y2, z2, jb, pb, sb, err)) {
+        if (!seg_slot(a, w, gsy, gsz, p, ba, sa, err) ||
+            !seg_slot(a, w, gsy2, gsz2, q, bb, sb, err)) {
             bad = true;
             return;
         }
         if (sa == last_sa && sb == last_sb) return;
         last_sa = sa;
         last_sb = sb;
-        gunion(F, slot_node(a, pa, sa), slot_node(a, pb, sb), budget, err);
+        gunion(F, slot_node(a, ba, sa), slot_node(a, bb, sb), budget, err);
     });
 }
 
 // ---------------------------------------------------------------------------
 // Kernel 3: link.  Resolve the brick's border roots to 1 + the key of their
 // global root and write every voxel's label.
-struct SmemVolLink {
-    __align__(16) int S[kNodes];   // label of each run node
-    int R[kSlots];                 // final label of each border root
-    uint32_t bits[kThreads];
+template <int R> struct SmemVolLink {
+    __align__(16) int S[kNodes];   // label of each segment
+    int Rt[kSlots];                // final label of each border root
+    uint32_t rows[R][kThreads];
     uint32_t st[kThreads];
     int base[kThreads];
 };
 
+template <int CONN>
 __global__ void __launch_bounds__(kThreads) kv_link(VolArgs a, int *err) {
-    __shared__ SmemVolLink sm;
+    constexpr int SY = Strip<CONN>::SY, SZ = Strip<CONN>::SZ, R = Strip<CONN>::R;
+    constexpr int BYR = kStrips * SY;
+    __shared__ SmemVolLink<R> sm;
     const Geom3 &g = a.g;
     const int t = threadIdx.x;
     const long long brick = blockIdx.x;
@@ -456,7 +600,7 @@ __global__ void __launch_bounds__(kThreads) kv_link(VolArgs a, int *err) {
     const int *bw = a.bws + (size_t)brick * kBrickInts;
     const int nb = min(__ldcg(bw), kSlots);
     const int nn = min(__ldcg(bw + 1), kNodes);
-    // node labels to shared memory, 16 bytes at a time (the source is 16-byte
+    // segment labels to shared memory, 16 bytes at a time (the source is 16-byte
     // aligned and rounding the count up stays inside the brick's workspace)
     for (int c = t; c < (nn + 3) / 4; c += kThreads) {
         const unsigned dst = (unsigned)__cvta_generic_to_shared(&sm.S[4 * c]);
@@ -465,12 +609,14 @@ __global__ void __launch_bounds__(kThreads) kv_link(VolArgs a, int *err) {
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
     {
-        const int ly = t % kBY, lz = t / kBY;
-        const int y = by * kBY + ly, z = bz * kBZ + lz;
-        const uint32_t bits =
-            (y < g.H && z < g.D) ? __ldcg(a.bits + ((size_t)z * g.H + y) * g.nwg + bx) : 0u;
-        sm.bits[t] = bits;
-        sm.st[t] = bits & ~(bits << 1);
+        const int gsy = by * kStrips + t % kStrips, gsz = bz * kStrips + t / kStrips;
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+            const int y = gsy * SY + rr % SY, z = gsz * SZ + rr / SY;
+            sm.rows[rr][t] =
+                (y < g.H && z < g.D) ? __ldcg(a.bits + ((size_t)z * g.H + y) * g.nwg + bx) : 0u;
+        }
+        sm.st[t] = (uint32_t)__ldcg(bw + kOffSt + t);
         sm.base[t] = __ldcg(reinterpret_cast<const uint16_t *>(bw + kOffBase) + t);
     }
     {
@@ -485,7 +631,7 @@ __global__ void __launch_bounds__(kThreads) kv_link(VolArgs a, int *err) {
                 if (p == r) break;
                 r = p;
             }
-            sm.R[j] = 1 + (int)(r >> (kBrickBits + kSlotBits));
+            sm.Rt[j] = 1 + (int)(r >> (kBrickBits + kSlotBits));
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -495,7 +641,7 @@ __global__ void __launch_bounds__(kThreads) kv_link(VolArgs a, int *err) {
         if (v < 0) {
             const int j = -v - 1;
             if (j < nb) {
-                sm.S[n] = sm.R[j];
+                sm.S[n] = sm.Rt[j];
             } else {
                 sm.S[n] = 0;
                 atomicOr(err, kErrBorderCap);
@@ -503,16 +649,19 @@ __global__ void __launch_bounds__(kThreads) kv_link(VolArgs a, int *err) {
         }
     }
     __syncthreads();
-    // 8 four-voxel chunks per row: a warp stores four whole 128-byte rows
+    // the brick's rows in raster order, 8 four-voxel chunks each: a warp stores
+    // four whole 128-byte rows
     const int x0 = 32 * bx;
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < R * 8; ++k) {
         const int idx = k * kThreads + t;
-        const int tr = idx >> 3, c = idx & 7;
-        const int y = by * kBY + tr % kBY, z = bz * kBZ + tr / kBY;
+        const int q = idx >> 3, c = idx & 7;
+        const int ly = q % BYR, lz = q / BYR;
+        const int y = by * BYR + ly, z = bz * kStrips * SZ + lz;
         const int xs = x0 + 4 * c;
         if (y >= g.H || z >= g.D || xs >= g.W) continue;
-        const uint32_t rb = sm.bits[tr], sq = sm.st[tr];
-        const int b0 = sm.base[tr];
+        const int ts = (lz / SZ) * kStrips + ly / SY, rr = (lz % SZ) * SY + ly % SY;
+        const uint32_t rb = sm.rows[rr][ts], sq = sm.st[ts];
+        const int b0 = sm.base[ts];
         int v[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -538,12 +687,12 @@ static void launch_volume(const VolArgs &a, int *err, cudaStream_t stream) {
     const unsigned nbricks = (unsigned)g.nbricks;
     kv_merge<CONN><<<nbricks, kThreads, 0, stream>>>(a, err);
     if (g.nwg > 1) {
-        const long long items = (long long)g.D * g.H * (g.nwg - 1);
+        const long long items = (long long)g.nsy * g.nsz * (g.nwg - 1);
         kv_xfaces<CONN><<<(unsigned)((items + 255) / 256), 256, 0, stream>>>(a, items, err);
     }
-    const long long yz = face_rows(g.D, g.H) * RowPairs<CONN>::n * g.nwg;
+    const long long yz = face_strips(g.nsz, g.nsy) * n_pairs<CONN>() * g.nwg;
     kv_yzfaces<CONN><<<(unsigned)((yz + 255) / 256), 256, 0, stream>>>(a, yz, err);
-    kv_link<<<nbricks, kThreads, 0, stream>>>(a, err);
+    kv_link<CONN><<<nbricks, kThreads, 0, stream>>>(a, err);
 }
 
 }  // namespace vol
@@ -551,8 +700,8 @@ static void launch_volume(const VolArgs &a, int *err, cudaStream_t stream) {
 
 extern "C" size_t ccl_workspace_bytes3d(int depth, int height, int width, int connectivity) {
     using namespace ccl::vol;
-    if (!valid_conn3(connectivity) || !dims_ok(depth, height, width)) return 0;
-    const Geom3 g = make_geom3(depth, height, width);
+    if (!valid_conn3(connectivity) || !dims_ok(depth, height, width, connectivity)) return 0;
+    const Geom3 g = make_geom3(depth, height, width, connectivity);
     return bits_bytes3(g) + bricks_bytes3(g) + par_bytes3(g);
 }
 
@@ -560,7 +709,8 @@ extern "C" ccl_status ccl_label3d(const uint8_t *d_vol, int32_t *d_labels, int d
                                   int width, int connectivity, void *d_ws, size_t ws_bytes,
                                   ccl_stream stream) {
     using namespace ccl::vol;
-    if (!d_vol || !d_labels || !valid_conn3(connectivity) || !dims_ok(depth, height, width))
+    if (!d_vol || !d_labels || !valid_conn3(connectivity) ||
+        !dims_ok(depth, height, width, connectivity))
         return CCL_ERR_INVALID_ARG;
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const size_t need = ccl_workspace_bytes3d(depth, height, width, connectivity);
@@ -574,7 +724,7 @@ extern "C" ccl_status ccl_label3d(const uint8_t *d_vol, int32_t *d_labels, int d
     int *err = ccl::device_error_word();
     if (!err) return CCL_ERR_CUDA;
     VolArgs a;
-    a.g = make_geom3(depth, height, width);
+    a.g = make_geom3(depth, height, width, connectivity);
     a.vol = d_vol;
     a.labels = d_labels;
     a.bits = static_cast<uint32_t *>(d_ws);

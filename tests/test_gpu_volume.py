@@ -91,7 +91,7 @@ def test_unaligned_input_and_reused_workspace():
     buf = torch.zeros(d * h * w + 1, dtype=torch.uint8, device=DEV)
     buf[1:] = torch.from_numpy(vol.ravel()).to(DEV)
     view = buf[1:].view(d, h, w)                       # 1-byte offset: unaligned loads
-    need = ccl.ccl_workspace_bytes3d(d, h, w, 26)
+    need = max(ccl.ccl_workspace_bytes3d(d, h, w, c) for c in CONNS)
     guard = 4096
     ws = torch.full((need + guard,), 0xA5, dtype=torch.uint8, device=DEV)
     for conn in CONNS:
