@@ -445,9 +445,10 @@ __device__ __forceinline__ gnode slot_node(const VolArgs &a, long long brick, in
 
 // ---------------------------------------------------------------------------
 // Kernel 2a: unions across x faces.  Item i = (strip, word w >= 1): the
-// segment at voxel 32w of the strip and the segments at x = 32w - 1 (in brick
-// w - 1) of every neighbour of a voxel 32w of the strip's rows.  Consecutive
-// neighbours of one border root are unioned once.
+// segment at voxel 32w of the strip and, for each neighbour strip, the segment
+// at x = 32w - 1 (in brick w - 1) when one of its rows holds a neighbour of a
+// voxel 32w of the strip's rows.  Consecutive neighbours of one border root
+// are unioned once.
 template <int CONN>
 __global__ void __launch_bounds__(256) kv_xfaces(VolArgs a, long long items, int *err) {
     constexpr int SY = Strip<CONN>::SY, SZ = Strip<CONN>::SZ, R = Strip<CONN>::R;
@@ -458,38 +459,53 @@ __global__ void __launch_bounds__(256) kv_xfaces(VolArgs a, long long items, int
     const int w = 1 + (int)(i % nw1);
     const long long sidx = i / nw1;
     const int gsy = (int)(sidx % g.nsy), gsz = (int)(sidx / g.nsy);
+    uint32_t amask = 0;   // rows of the strip whose voxel 32w is set
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+        const int y = gsy * SY + rr % SY, z = gsz * SZ + rr / SY;
+        if (y < g.H && z < g.D && (__ldcg(a.bits + ((size_t)z * g.H + y) * g.nwg + w) & 1u))
+            amask |= 1u << rr;
+    }
+    if (!amask) return;
     const Forest3 F{a.par};
     int budget = kGlobHopBudget;
     gnode self = kNoNode;
     long long last_brick = -1;
     int last_slot = -1;
+    for (int dsz = -1; dsz <= 1; ++dsz)
+        for (int dsy = -1; dsy <= 1; ++dsy) {
+            const int gsy2 = gsy + dsy, gsz2 = gsz + dsz;
+            if (gsy2 < 0 || gsy2 >= g.nsy || gsz2 < 0 || gsz2 >= g.nsz) continue;
+            bool adj = false;
 #pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-        const int y = gsy * SY + rr % SY, z = gsz * SZ + rr / SY;
-        if (y >= g.H || z >= g.D) continue;
-        if (!(__ldcg(a.bits + ((size_t)z * g.H + y) * g.nwg + w) & 1u)) continue;
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy) {
-                if (!x_pair<CONN>(dy, dz)) continue;
-                const int y2 = y + dy, z2 = z + dz;
-                if (y2 < 0 || y2 >= g.H || z2 < 0 || z2 >= g.D) continue;
-                const uint32_t b = __ldcg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + (w - 1));
-                if (!(b >> 31)) continue;
-                long long ob;
-                int os;
-                if (!seg_slot(a, w - 1, y2 / SY, z2 / SZ, 31, ob, os, err)) return;
-                if (ob == last_brick && os == last_slot) continue;
-                last_brick = ob;
-                last_slot = os;
-                if (self == kNoNode) {
-                    long long sb;
-                    int ss;
-                    if (!seg_slot(a, w, gsy, gsz, 0, sb, ss, err)) return;
-                    self = slot_node(a, sb, ss);
+            for (int r2 = 0; r2 < R; ++r2) {
+                const int y2 = gsy2 * SY + r2 % SY, z2 = gsz2 * SZ + r2 / SY;
+                if (y2 >= g.H || z2 >= g.D) continue;
+                bool near = false;   // a set row of the strip neighbours row r2 at dx = 1
+#pragma unroll
+                for (int rr = 0; rr < R; ++rr) {
+                    const int dy = y2 - (gsy * SY + rr % SY), dz = z2 - (gsz * SZ + rr / SY);
+                    near |= ((amask >> rr) & 1u) && dy >= -1 && dy <= 1 && dz >= -1 &&
+                            dz <= 1 && x_pair<CONN>(dy, dz);
                 }
-                gunion(F, self, slot_node(a, ob, os), budget, err);
+                if (near && (__ldcg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + (w - 1)) >> 31))
+                    adj = true;
             }
-    }
+            if (!adj) continue;
+            long long ob;
+            int os;
+            if (!seg_slot(a, w - 1, gsy2, gsz2, 31, ob, os, err)) return;
+            if (ob == last_brick && os == last_slot) continue;
+            last_brick = ob;
+            last_slot = os;
+            if (self == kNoNode) {
+                long long sb;
+                int ss;
+                if (!seg_slot(a, w, gsy, gsz, 0, sb, ss, err)) return;
+                self = slot_node(a, sb, ss);
+            }
+            gunion(F, self, slot_node(a, ob, os), budget, err);
+        }
 }
 
 // Strips that may pair with a strip of another brick along y or z: strip y
