@@ -509,7 +509,8 @@ def volume_leg(dev, stream, reps: int = 20, side: int = 512, p: float = 0.5,
     vol = torch.from_numpy(synthetic.bernoulli3d(side, side, side, p, 0)).to(dev)
     out = torch.empty((side, side, side), dtype=torch.int32, device=dev)
     res = {"shape": [side, side, side], "density": p,
-           "what": "3-D labelling (bricks of 32x16x16 voxels), labels 1 + smallest voxel index"}
+           "what": "3-D labelling (bricks of 16x16 strips of 1, 2 or 2x2 rows by 32 voxels), "
+                   "labels 1 + smallest voxel index"}
     for conn in conns:
         ws = torch.empty(ccl.ccl_workspace_bytes3d(side, side, side, conn), dtype=torch.uint8,
                          device=dev)
