@@ -249,6 +249,36 @@ def test_component_stats_closed_forms():
     assert cb["count"].size == h * w // 2 and set(cb["count"].tolist()) == {1}
 
 
+@pytest.mark.parametrize("conn", [4, 8])
+def test_component_stats_against_scipy(conn):
+    """Library special case: scipy.ndimage's per-label sums, bounding slices and
+    centres of mass over the same labels."""
+    from scipy import ndimage
+
+    for seed in range(4):
+        img = synthetic.bernoulli(150 + 7 * seed, 230, 0.3 + 0.1 * seed, seed, cfg_id=65)
+        lab = oracle.label(img, conn)
+        st = oracle.component_stats(lab)
+        idx = st["label"]
+        ones = np.ones(lab.shape, np.int64)
+        np.testing.assert_array_equal(ndimage.sum_labels(ones, lab, idx).astype(np.int64),
+                                      st["count"])
+        ys, xs = np.indices(lab.shape)
+        np.testing.assert_array_equal(ndimage.sum_labels(xs, lab, idx).astype(np.int64),
+                                      st["sum_x"])
+        np.testing.assert_array_equal(ndimage.sum_labels(ys, lab, idx).astype(np.int64),
+                                      st["sum_y"])
+        # find_objects indexes slices by label value: entry L - 1 for label L
+        boxes = ndimage.find_objects(lab)
+        for k, L in enumerate(idx.tolist()):
+            sy, sx = boxes[L - 1]
+            assert (st["ymin"][k], st["ymax"][k]) == (sy.start, sy.stop - 1)
+            assert (st["xmin"][k], st["xmax"][k]) == (sx.start, sx.stop - 1)
+        com = np.array(ndimage.center_of_mass(ones, lab, idx))
+        np.testing.assert_allclose(com[:, 0], st["sum_y"] / st["count"], rtol=0, atol=1e-9)
+        np.testing.assert_allclose(com[:, 1], st["sum_x"] / st["count"], rtol=0, atol=1e-9)
+
+
 # ---------------------------------------------------------------------------
 # label_regions: every equal-value region (the paper's equality predicate,
 # §II-A row/column scans and §II-B boundary tests)
