@@ -149,9 +149,11 @@ ccl_status ccl_label_regions(const uint8_t *d_img, int32_t *d_labels, int height
 
 /* ---- volumes ---------------------------------------------------------------
  * Label a 3-D volume (the paper's "2D/3D grid", §I) with the three phases one
- * dimension up: a shared-memory local merge per brick of 32 x 16 x 16 voxels
- * (Kernel 1, §II-A), unions across brick faces (Kernel 2, §II-B) and a link
- * pass (§II-C).
+ * dimension up: a shared-memory local merge per brick (Kernel 1, §II-A),
+ * unions across brick faces (Kernel 2, §II-B) and a link pass (§II-C).  A
+ * brick is 32 voxels along x by 16 x 16 strips, a strip being 1 row (6), 2 rows
+ * along y (18) or 2 x 2 rows (26): 32 x 16 x 16, 32 x 32 x 16 or 32 x 32 x 32
+ * voxels.
  *   d_vol    : device, depth*height*width bytes, voxel (x, y, z) at index
  *              (z*height + y)*width + x, nonzero = foreground (read only)
  *   d_labels : device, depth*height*width int32, fully overwritten: 0 for
@@ -163,7 +165,8 @@ ccl_status ccl_label_regions(const uint8_t *d_img, int32_t *d_labels, int height
  *              256-byte aligned, or NULL (library-owned, as for ccl_label)
  *   stream   : CUDA stream to enqueue on
  * Limits: depth*height*width <= 2^31 - 2 and at most 2^22 bricks
- * (ceil(width/32) * ceil(height/16) * ceil(depth/16)).  Returns CCL_OK once
+ * (ceil(width/32) * ceil(height/bh) * ceil(depth/bd) for a brick of
+ * 32 x bh x bd voxels).  Returns CCL_OK once
  * the three kernels are enqueued; CCL_ERR_INVALID_ARG for NULL pointers, bad
  * sizes or connectivity, or a workspace that is too small or misaligned;
  * CCL_ERR_OOM / CCL_ERR_CUDA otherwise.  Device-side failures are reported by
@@ -171,7 +174,8 @@ ccl_status ccl_label_regions(const uint8_t *d_img, int32_t *d_labels, int height
 ccl_status ccl_label3d(const uint8_t *d_vol, int32_t *d_labels, int depth, int height, int width,
                        int connectivity, void *d_ws, size_t ws_bytes, ccl_stream stream);
 
-/* Bytes of workspace ccl_label3d needs (0 on invalid arguments). */
+/* Bytes of workspace ccl_label3d needs for this size and connectivity (the
+ * brick shape depends on the connectivity); 0 on invalid arguments. */
 size_t ccl_workspace_bytes3d(int depth, int height, int width, int connectivity);
 
 /* Number of unordered pairs of neighbouring pixels that lie in different
