@@ -181,3 +181,17 @@ def test_tile_table_get_set_roundtrip(lib):
 
 def before_4096(lib):
     return lib.ccl_default_tile_width(4096, 4096, 4)
+
+
+def test_binding_rejects_host_tensors_and_bad_shapes(lib):
+    """The Python binding checks tensors before any library call: host tensors
+    and wrong dtypes or ranks raise TypeError."""
+    import torch
+
+    img = torch.zeros((8, 8), dtype=torch.uint8)
+    vol = torch.zeros((4, 4, 4), dtype=torch.uint8)
+    for call in (lambda: ccl.ccl_label(img, 8), lambda: ccl.ccl_label_regions(img, (0, 1), 8),
+                 lambda: ccl.ccl_label3d(vol, 26), lambda: ccl.ccl_label3d(img, 6),
+                 lambda: ccl.ccl_label(img.float(), 8)):
+        with pytest.raises(TypeError):
+            call()
