@@ -288,21 +288,35 @@ def e2e_server(img_np, steps: int, device_index: int):
             srv.wait(rid)
         dt = time.perf_counter() - t0
         stats = srv.stats()
+        split = srv.timing()
     return {"value": n * H * W / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": H * W,
             "d2h_bytes_per_step": 4 * H * W, "requests": n,
-            "server_p50_ms": stats["p50_ms"], "server_p99_ms": stats["p99_ms"]}
+            "server_p50_ms": stats["p50_ms"], "server_p99_ms": stats["p99_ms"],
+            "per_request_ms": {"h2d": round(split["h2d_ms"], 4), "label": round(split["label_ms"], 4),
+                               "d2h": round(split["d2h_ms"], 4)},
+            "copy_gb_s": {"h2d": round(H * W / max(split["h2d_ms"], 1e-9) / 1e6, 1),
+                          "d2h": round(4 * H * W / max(split["d2h_ms"], 1e-9) / 1e6, 1)},
+            "what": "each request: host-to-device copy, labelling, device-to-host copy on one "
+                    "worker stream (CUDA events); three workers overlap requests"}
 
 
 def batched_vs_plain(device_index: int, seed: int = 0, reps: int = 10):
     """The batched configuration: 256 images, sides log-uniform in 64..2048,
     p ~ U(0.3, 0.7), 8-connectivity.  One batched call (graph replay) against
-    256 plain ccl_label calls on one stream, device time by CUDA events, median
-    of `reps`."""
+    256 plain ccl_label calls on one stream.  Both go through the C ABI with
+    their arguments built beforehand (a C caller's cost, not the Python
+    binding's), `reps` batches back to back between CUDA events, so that the
+    device time is not diluted by host preparation; also the host latency of
+    one synchronised batched call."""
+    import ctypes
+
     import torch
 
     import paper_1708_08180_gb300 as ccl
+    from paper_1708_08180_gb300 import _lib
     import synthetic
 
+    lib = _lib.load()
     dev = torch.device("cuda", device_index)
     host = synthetic.batch_images(seed)
     imgs = [torch.from_numpy(h).to(dev) for h in host]
@@ -312,39 +326,64 @@ def batched_vs_plain(device_index: int, seed: int = 0, reps: int = 10):
     ws_p = torch.empty(max(ccl.ccl_workspace_bytes(*h.shape, 8) for h in host),
                        dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-
-    def time_it(fn):
-        ts = []
-        for r in range(reps + 2):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            b.synchronize()
-            if r >= 2:
-                ts.append(a.elapsed_time(b))
-        ts.sort()
-        return ts[len(ts) // 2], ts[min(len(ts) - 1, int(round(0.99 * (len(ts) - 1))))]
-
-    def plain():
-        for i, o in zip(imgs, outs):
-            ccl.ccl_label(i, 8, out=o, ws=ws_p, stream=stream)
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    arr = (_lib.ccl_image * len(imgs))()
+    for k, (im, o) in enumerate(zip(imgs, outs)):
+        arr[k].d_img, arr[k].d_labels = im.data_ptr(), o.data_ptr()
+        arr[k].height, arr[k].width = im.shape[0], im.shape[1]
+    plain_args = [(ctypes.c_void_p(im.data_ptr()), ctypes.c_void_p(o.data_ptr()), im.shape[0],
+                   im.shape[1]) for im, o in zip(imgs, outs)]
+    wsb_p, wsb_n = ctypes.c_void_p(ws_b.data_ptr()), ws_b.numel()
+    wsp_p, wsp_n = ctypes.c_void_p(ws_p.data_ptr()), ws_p.numel()
 
     def batched():
-        ccl.ccl_label_batched(imgs, 8, outs=outs, ws=ws_b, stream=stream)
+        st = lib.ccl_label_batched(arr, len(imgs), 8, wsb_p, wsb_n, sh)
+        if st:
+            raise ccl.CclError(st, "ccl_label_batched")
 
-    tb, tb99 = time_it(batched)
-    tp, tp99 = time_it(plain)
+    def plain():
+        for a, b, h, w in plain_args:
+            st = lib.ccl_label(a, b, h, w, 8, wsp_p, wsp_n, sh)
+            if st:
+                raise ccl.CclError(st, "ccl_label")
+
+    def time_it(fn):
+        fn()
+        fn()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    tb = time_it(batched)
+    tp = time_it(plain)
+    lat = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        batched()
+        stream.synchronize()
+        lat.append((time.perf_counter() - t0) * 1e3)
     ccl.ccl_sync(stream)
+    lat.sort()
+    peak, _ = hbm_peak()
     return {"images": len(host), "pixels": px,
-            "batched_gpix_s": px / (tb / 1e3) / 1e9, "batched_ms": tb, "batched_p99_ms": tb99,
-            "plain_gpix_s": px / (tp / 1e3) / 1e9, "plain_ms": tp, "plain_p99_ms": tp99,
-            "speedup": tp / tb}
+            "batched_gpix_s": px / (tb / 1e3) / 1e9, "batched_ms": tb,
+            "batched_path_frac_5B": round(5 * px / (tb / 1e3) / 1e9 / peak, 4),
+            "batched_sync_latency_ms_p50": lat[len(lat) // 2], "batched_sync_latency_ms_max": lat[-1],
+            "plain_gpix_s": px / (tp / 1e3) / 1e9, "plain_ms": tp,
+            "speedup": tp / tb,
+            "what": "device time per batch (CUDA events around %d back-to-back batches), "
+                    "C ABI with prebuilt arguments; sync latency = one call + stream synchronise "
+                    "on the host clock" % reps}
 
 
-def served_vs_plain(device_index: int, rates=(2000.0, 10000.0), seconds: float = 1.0,
-                    seed: int = 0):
+def served_vs_plain(device_index: int, rates=(1000.0, 5000.0, 20000.0), seconds: float = 1.0,
+                    seed: int = 0, max_requests: int = 0):
     """Serving: Poisson arrivals; 50 % 1920x1080 smoothed-noise video frames,
     50 % squares log-uniform 128..4096, Bernoulli 0.5, 8-connectivity.  The
     continuous-batching server against one plain call per request (H2D,
@@ -368,7 +407,10 @@ def served_vs_plain(device_index: int, rates=(2000.0, 10000.0), seconds: float =
                 for k, v in pool.items()}
     out = {}
     for rate in rates:
-        trace = synthetic.serving_trace(rate, max(1, int(rate * seconds)), seed)
+        count = max(1, int(rate * seconds))
+        if max_requests > 0:
+            count = min(count, max_requests)
+        trace = synthetic.serving_trace(rate, count, seed)
         items = []
         for k, (t_arr, kind, h, w) in enumerate(trace):
             j = k % 16
@@ -402,12 +444,15 @@ def served_vs_plain(device_index: int, rates=(2000.0, 10000.0), seconds: float =
                 lat[k] = (done_t[k] - items[k][0]) * 1e3
             span = max(done_t) - items[0][0]
             native = srv.stats()
+            split = srv.timing()
         # client side: scheduled arrival -> labels in host memory, seen by a
         # Python thread that waits in arrival order; native: the server's own
         # submit -> completion clock (C++ steady_clock, no interpreter in it)
         srv_res = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                    "gpix_s": px / span / 1e9,
-                   "native_p50_ms": native.get("p50_ms"), "native_p99_ms": native.get("p99_ms")}
+                   "native_p50_ms": native.get("p50_ms"), "native_p99_ms": native.get("p99_ms"),
+                   "per_batch_ms": {k: round(v, 4) for k, v in split.items() if k != "batches"},
+                   "batches": split["batches"]}
 
         # plain: one ccl_label per request, in arrival order, one stream
         stream = torch.cuda.Stream(dev)
@@ -439,6 +484,92 @@ def served_vs_plain(device_index: int, rates=(2000.0, 10000.0), seconds: float =
             "plain": {"p50_ms": float(np.percentile(lat_p, 50)),
                       "p99_ms": float(np.percentile(lat_p, 99)), "gpix_s": px / span_p / 1e9}}
     return out
+
+
+def flush_l2(buf):
+    """Overwrite a buffer larger than L2 so that the next call reads from HBM."""
+    buf.add_(1)
+
+
+def small_leg(dev, stream, reps: int = 200):
+    """The 512 x 512 workload (Bernoulli 0.5, 8-connectivity), seeds 0-9:
+    back-to-back calls on one stream (throughput, CUDA events around `reps`
+    calls per image) and single calls each followed by a device synchronise
+    (latency, wall clock).  The inputs fit in L2 at this size, so the roofline
+    fraction is informational only."""
+    import torch
+
+    import paper_1708_08180_gb300 as ccl
+    import synthetic
+
+    n = 512
+    imgs = [torch.from_numpy(synthetic.bernoulli(n, n, 0.5, sd, cfg_id=synthetic.CFG_SMALL)).to(dev)
+            for sd in range(10)]
+    out = torch.empty((n, n), dtype=torch.int32, device=dev)
+    ws = torch.empty(ccl.ccl_workspace_bytes(n, n, 8), dtype=torch.uint8, device=dev)
+    per_img, lat = [], []
+    for im in imgs:
+        for _ in range(5):
+            ccl.ccl_label(im, 8, out=out, ws=ws, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ccl.ccl_label(im, 8, out=out, ws=ws, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        per_img.append(e0.elapsed_time(e1) / reps)
+        for _ in range(20):
+            t0 = time.perf_counter()
+            ccl.ccl_label(im, 8, out=out, ws=ws, stream=stream)
+            stream.synchronize()
+            lat.append((time.perf_counter() - t0) * 1e3)
+    ccl.ccl_sync(stream)
+    ms = statistics.median(per_img)
+    peak, _ = hbm_peak()
+    return {"shape": [n, n], "density": 0.5, "conn": 8, "seeds": 10,
+            "back_to_back_us": round(ms * 1e3, 2), "gpix_s": round(n * n / (ms / 1e3) / 1e9, 3),
+            "path_frac_5B": round(5 * n * n / (ms / 1e3) / 1e9 / peak, 5),
+            "sync_latency_p50_us": round(statistics.median(lat) * 1e3, 1),
+            "sync_latency_p99_us": round(sorted(lat)[int(0.99 * (len(lat) - 1))] * 1e3, 1),
+            "what": "per-call device time back to back (events) and host-synchronised latency"}
+
+
+def structured_leg(dev, stream, reps: int = 10):
+    """The structured 4096 x 4096 workload at both connectivities: block noise
+    with g in {1, 2, 4, 8, 16}, the serpentine and its transpose, 64 concentric
+    rings, full and empty.  Each image: `reps` calls, each timed with CUDA
+    events after an L2 flush (a 256 MiB buffer overwritten), median."""
+    import torch
+
+    import paper_1708_08180_gb300 as ccl
+    import synthetic
+
+    n = 4096
+    flush = torch.zeros(64 << 20, dtype=torch.int32, device=dev)
+    out = torch.empty((n, n), dtype=torch.int32, device=dev)
+    res = {}
+    for name, img in synthetic.structured_set(n, n):
+        dimg = torch.from_numpy(img).to(dev)
+        for conn in (4, 8):
+            ws = torch.empty(ccl.ccl_workspace_bytes(n, n, conn), dtype=torch.uint8, device=dev)
+            ccl.ccl_label(dimg, conn, out=out, ws=ws, stream=stream)
+            ts = []
+            for _ in range(reps):
+                flush_l2(flush)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ccl.ccl_label(dimg, conn, out=out, ws=ws, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            res[f"{name}_conn{conn}"] = {"ms": round(ms, 4),
+                                         "gpix_s": round(n * n / (ms / 1e3) / 1e9, 2)}
+    ccl.ccl_sync(stream)
+    return {"shape": [n, n], "images": res,
+            "what": "device time per call after an L2 flush, median of %d" % reps}
 
 
 def stats_leg(labels, stream, reps: int = 50):
@@ -580,18 +711,33 @@ def run_ours(args, rank, world, local):
     sampler.start()
     time.sleep(0.3)
 
-    barrier(world, dev)
-    torch.cuda.synchronize(dev)
-    t_wall0 = time.time()
+    # The K timed steps are repeated back to back until the timed region spans
+    # at least --min-timed-s of wall time, so that the clock sampler (100 ms
+    # period) sees it; ms_per_step is the median repetition's K-step time / K.
     start.record(stream)
     for k in range(K):
         ccl.ccl_label(imgs[k % ROTATE], CONN, out=outs[k % ROTATE], ws=wss[k % ROTATE],
                       stream=stream)
     end.record(stream)
     torch.cuda.synchronize(dev)
+    est_ms = max(start.elapsed_time(end), 1e-3)
+    reps = max(1, min(100000, int(-(-args.min_timed_s * 1e3 // est_ms))))
+    rep_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+    barrier(world, dev)
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.time()
+    for e0, e1 in rep_ev:
+        e0.record(stream)
+        for k in range(K):
+            ccl.ccl_label(imgs[k % ROTATE], CONN, out=outs[k % ROTATE], ws=wss[k % ROTATE],
+                          stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
     t_wall1 = time.time()
     barrier(world, dev)
     ccl.ccl_sync(stream)
+    rep_ms = sorted(e0.elapsed_time(e1) for e0, e1 in rep_ev)
     # the per-kernel loop, same work, events around each kernel
     for k in range(KP):
         ccl.ccl_set_phase_events(ev[k])
@@ -602,7 +748,7 @@ def run_ours(args, rank, world, local):
     ccl.ccl_sync(stream)
     sampler.stop()
 
-    ms_local = start.elapsed_time(end)
+    ms_local = rep_ms[len(rep_ms) // 2]
     ms_total = reduce_max(ms_local, world, dev)
     phase = {name: [] for name in KERNELS}
     for k in range(KP):
@@ -663,11 +809,20 @@ def run_ours(args, rank, world, local):
                    "l2": f"{ROTATE} distinct inputs/outputs/workspaces rotated per step "
                          f"({ROTATE} x 320 MiB > 129 MB L2), no flush"},
         "roofline": roofline,
-        "gpu_launches": 3 * K,
+        "gpu_launches": 3 * K * reps,
         "clocks": clocks,
+        "timing": {"repetitions_of_K_steps": reps, "rep_ms_min": round(rep_ms[0], 5),
+                   "rep_ms_median": round(ms_local, 5), "rep_ms_max": round(rep_ms[-1], 5),
+                   "timed_region_s": round(t_wall1 - t_wall0, 3),
+                   "what": "the K timed steps repeated back to back so that the clock samples "
+                           "cover the timed region; ms_per_step = median repetition / K"},
     }
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e_server(host_imgs[0], K, local)
+    if rank == 0 and not args.no_small:
+        line["small_512"] = small_leg(dev, stream)
+    if rank == 0 and not args.no_structured:
+        line["structured_4096"] = structured_leg(dev, stream)
     if rank == 0 and not args.no_stats:
         line["component_stats"] = stats_leg(outs[0], stream)
     if rank == 0 and not args.no_volume:
@@ -699,7 +854,14 @@ def main(argv=None) -> int:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stats", action="store_true", help="skip the component-statistics leg")
+    ap.add_argument("--no-small", action="store_true", help="skip the 512x512 leg")
+    ap.add_argument("--no-structured", action="store_true",
+                    help="skip the structured 4096x4096 leg")
     ap.add_argument("--no-volume", action="store_true", help="skip the 3-D volume leg")
+    ap.add_argument("--served-full", action="store_true",
+                    help="run only the serving sweep (1k-20k req/s, 10 s or 20k requests each)")
+    ap.add_argument("--cpu-sweep", action="store_true",
+                    help="run only the CPU oracle over the density sweep and structured set")
     ap.add_argument("--volume-only", action="store_true",
                     help="run only the 3-D volume leg (one JSON line), e.g. for profiling")
     ap.add_argument("--volume-side", type=int, default=512, help="volume side (default 512)")
@@ -712,6 +874,9 @@ def main(argv=None) -> int:
                     help="skip the batched-vs-plain leg (256 images of 64..2048)")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the served-vs-plain leg (Poisson arrivals)")
+    ap.add_argument("--min-timed-s", type=float, default=1.5,
+                    help="repeat the K timed steps until the timed region lasts this long "
+                         "(clock samples need it); the median repetition is reported")
     ap.add_argument("--phase-steps", type=int, default=1000,
                     help="steps of the second, per-kernel timed loop (0: skip it)")
     ap.add_argument("--size", type=int, default=8192, help="image side (default 8192)")
@@ -732,7 +897,71 @@ def main(argv=None) -> int:
         return run_reference(args, rank, world)
     if args.volume_only:
         return run_volume_only(args, local)
+    if args.served_full:
+        return run_served_full(args, local)
+    if args.cpu_sweep:
+        return run_cpu_sweep(args)
     return run_ours(args, rank, world, local)
+
+
+def run_served_full(args, local) -> int:
+    """The serving workload at every rate of its sweep (1k, 2k, 5k, 10k, 20k
+    requests/s), each run for 10 s of arrivals or 20,000 requests, whichever
+    comes first: server vs one plain call per request, one JSON line."""
+    import torch
+
+    import paper_1708_08180_gb300 as ccl
+
+    torch.cuda.set_device(local)
+    ccl.load()
+    res = served_vs_plain(local, rates=(1000.0, 2000.0, 5000.0, 10000.0, 20000.0),
+                          seconds=10.0, max_requests=20000)
+    print(json.dumps({"served_full": res}), flush=True)
+    return 0
+
+
+def run_cpu_sweep(args) -> int:
+    """The CPU oracle (single-threaded breadth-first labelling) over the
+    plain-path sweep -- 1024^2 ... 8192^2 x p = 0.1 ... 0.9 x 4/8-connectivity,
+    seed 0 -- and the structured 4096^2 set, each the median of 3 runs, in
+    Mpixels/s; with the host's core count and CPU model."""
+    import platform
+
+    import oracle
+    import synthetic
+
+    oracle.label(synthetic.bernoulli(64, 64, 0.5, 0), 8)     # build/load outside the timing
+
+    def med3(img, conn):
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            oracle.label(img, conn)
+            ts.append(time.perf_counter() - t0)
+        return img.size / statistics.median(ts) / 1e6
+
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    out = {"cores_used": 1, "nproc": os.cpu_count(), "cpu": model, "machine": platform.machine(),
+           "unit": "Mpixels/s", "sweep": {}, "structured_4096": {}}
+    for n in (1024, 2048, 4096, 8192):
+        for k in range(1, 10):
+            p = k / 10
+            img = synthetic.bernoulli(n, n, p, 0)
+            for conn in (4, 8):
+                out["sweep"][f"{n}_p{p:.1f}_conn{conn}"] = round(med3(img, conn), 2)
+    for name, img in synthetic.structured_set(4096, 4096):
+        for conn in (4, 8):
+            out["structured_4096"][f"{name}_conn{conn}"] = round(med3(img, conn), 2)
+    print(json.dumps({"cpu_sweep": out}), flush=True)
+    return 0
 
 
 def run_volume_only(args, local) -> int:

@@ -201,6 +201,28 @@ ccl_status ccl_sync(ccl_stream stream);
 /* Free library-owned workspaces and batched-path state on every device. */
 ccl_status ccl_shutdown(void);
 
+/* ---- failure injection (for tests of the failure paths) ------------------
+ * The paper has no counterpart.  These calls let a test drive the library's
+ * failure detection without faulting a GPU.
+ *
+ * ccl_set_hop_budget: every union-find walk of the 2-D kernels (ccl_label,
+ * ccl_label_tiled, ccl_label_regions, ccl_label_batched and the server) draws
+ * on a per-thread budget of pointer hops -- smem_hops for the shared-memory
+ * forest of a tile, global_hops for the global forest of border roots.  When
+ * a budget runs out the thread sets the device error word and stops walking,
+ * so the kernel returns and ccl_sync() reports CCL_ERR_TIMEOUT (the labels of
+ * that call are then unspecified).  The defaults (2^20 hops each) are far
+ * above what any valid input needs; a test lowers them to make a walk run out
+ * on purpose.  0 restores a default.  The setting is process-wide and applies
+ * to calls enqueued after it.  CCL_ERR_INVALID_ARG for negative values.
+ *
+ * ccl_inject_alloc_failures: the next `count` library-owned workspace
+ * allocations (the ones made when a call is given d_ws = NULL) fail as if the
+ * device were out of memory: the call returns CCL_ERR_OOM and enqueues
+ * nothing.  0 clears pending failures.  CCL_ERR_INVALID_ARG if count < 0. */
+ccl_status ccl_set_hop_budget(int smem_hops, int global_hops);
+ccl_status ccl_inject_alloc_failures(int count);
+
 /* Allocation-free variant of ccl_label (the paper has no counterpart; it
  * exists for callers that cannot allocate device memory: code inside a host
  * framework that owns every device allocation through its own allocator,
@@ -317,7 +339,10 @@ ccl_status ccl_server_create(const ccl_server_config *cfg, ccl_server **out);
  * h_labels_out (height*width int32) are HOST buffers owned by the caller that
  * must stay valid until ccl_server_wait/poll reports completion.  A request
  * larger than the whole budget returns CCL_ERR_REJECTED; smaller ones wait
- * until enough budget is free.  *req_id_out receives the request id. */
+ * until enough budget is free.  Batches take queued requests in FIFO order
+ * and may look up to 32 entries past one that does not fit the free budget;
+ * a request passed over 8 times is admitted before any request behind it.
+ * *req_id_out receives the request id. */
 ccl_status ccl_server_submit(ccl_server *srv, const uint8_t *h_img, int height, int width,
                              int32_t *h_labels_out, uint64_t *req_id_out);
 
@@ -333,6 +358,14 @@ ccl_status ccl_server_poll(ccl_server *srv, uint64_t req_id);
  * host memory), Gpixel/s of completed work over the busy interval, counts. */
 ccl_status ccl_server_stats(ccl_server *srv, double *p50_ms, double *p99_ms,
                             double *gpix_per_s, uint64_t *completed, uint64_t *rejected);
+
+/* Where a batch's time goes, as means over the batches completed so far:
+ * host-to-device copies, the labelling launch and device-to-host copies of
+ * one batch, each measured with CUDA events on the batch's stream (batches of
+ * different workers overlap, so the three need not add up to the latency).
+ * Any output pointer may be NULL. */
+ccl_status ccl_server_timing(ccl_server *srv, double *h2d_ms, double *label_ms, double *d2h_ms,
+                             uint64_t *batches);
 
 /* Stop accepting, finish every admitted request, release all resources. */
 ccl_status ccl_server_destroy(ccl_server *srv);

@@ -27,6 +27,7 @@ __all__ = [
     "ccl_get_tile_table", "ccl_set_tile_table", "ccl_autotune", "load",
     "ccl_stats_workspace_bytes", "ccl_component_stats", "component_stats", "COMPONENT_FIELDS",
     "ccl_label_regions", "label_regions", "ccl_label3d", "ccl_workspace_bytes3d", "label3d",
+    "ccl_set_hop_budget", "ccl_inject_alloc_failures",
 ]
 
 # ccl_component as int32 words: label, count, xmin, ymin, xmax, ymax, then the
@@ -54,6 +55,26 @@ def _check_img(img):
         raise TypeError("image must be a CUDA tensor")
     if img.dtype != torch.uint8 or img.dim() != 2 or not img.is_contiguous():
         raise TypeError("image must be a contiguous 2-D uint8 tensor")
+
+
+def _check_out(out, shape, device, what: str = "out"):
+    """A caller-given output must be a contiguous int32 CUDA tensor of the given
+    shape on the input's device: the library writes through its pointer."""
+    torch = _torch()
+    if not isinstance(out, torch.Tensor) or not out.is_cuda or out.device != device:
+        raise TypeError(f"{what} must be a CUDA tensor on {device}")
+    if out.dtype != torch.int32 or tuple(out.shape) != tuple(shape) or not out.is_contiguous():
+        raise TypeError(f"{what} must be a contiguous int32 tensor of shape {tuple(shape)}")
+
+
+def _check_ws(ws, device):
+    """A caller-given workspace must be a contiguous uint8 CUDA tensor on the
+    input's device; its byte size is passed to the library, which checks it."""
+    torch = _torch()
+    if not isinstance(ws, torch.Tensor) or not ws.is_cuda or ws.device != device:
+        raise TypeError(f"ws must be a CUDA tensor on {device}")
+    if ws.dtype != torch.uint8 or not ws.is_contiguous():
+        raise TypeError("ws must be a contiguous uint8 tensor")
 
 
 def ccl_status_string(status: int) -> str:
@@ -92,13 +113,15 @@ def ccl_label_tiled(img, conn: int = 8, tile_w: int = 0, flags: int = 0, out=Non
     h, w = img.shape
     if out is None:
         out = torch.empty((h, w), dtype=torch.int32, device=img.device)
-    elif out.dtype != torch.int32 or tuple(out.shape) != (h, w) or not out.is_contiguous():
-        raise TypeError("out must be a contiguous int32 tensor shaped like img")
+    else:
+        _check_out(out, (h, w), img.device)
     need = ccl_workspace_bytes_tiled(h, w, conn, tile_w)
     if need == 0:
         raise CclError(1, "ccl_workspace_bytes_tiled")
     if ws is None:
         ws = _workspace(need, img.device)
+    else:
+        _check_ws(ws, img.device)
     with torch.cuda.device(img.device):
         st = load().ccl_label_tiled(img.data_ptr(), out.data_ptr(), h, w, conn, tile_w, flags,
                                     ws.data_ptr(), ws.numel(), _stream_handle(stream))
@@ -113,11 +136,15 @@ def ccl_label(img, conn: int = 8, out=None, ws=None, stream=None):
     h, w = img.shape
     if out is None:
         out = torch.empty((h, w), dtype=torch.int32, device=img.device)
+    else:
+        _check_out(out, (h, w), img.device)
     need = ccl_workspace_bytes(h, w, conn)
     if need == 0:
         raise CclError(1, "ccl_workspace_bytes")
     if ws is None:
         ws = _workspace(need, img.device)
+    else:
+        _check_ws(ws, img.device)
     with torch.cuda.device(img.device):
         st = load().ccl_label(img.data_ptr(), out.data_ptr(), h, w, conn, ws.data_ptr(),
                               ws.numel(), _stream_handle(stream))
@@ -139,13 +166,15 @@ def ccl_label_regions(img, levels: Sequence[int], conn: int = 8, out=None, ws=No
         raise ValueError("levels must be 1..256 byte values")
     if out is None:
         out = torch.empty((h, w), dtype=torch.int32, device=img.device)
-    elif out.dtype != torch.int32 or tuple(out.shape) != (h, w) or not out.is_contiguous():
-        raise TypeError("out must be a contiguous int32 tensor shaped like img")
+    else:
+        _check_out(out, (h, w), img.device)
     need = ccl_workspace_bytes(h, w, conn)
     if need == 0:
         raise CclError(1, "ccl_workspace_bytes")
     if ws is None:
         ws = _workspace(need, img.device)
+    else:
+        _check_ws(ws, img.device)
     host_levels = (ctypes.c_uint8 * len(lv))(*lv)
     with torch.cuda.device(img.device):
         st = load().ccl_label_regions(img.data_ptr(), out.data_ptr(), h, w, conn,
@@ -179,13 +208,15 @@ def ccl_label3d(vol, conn: int = 26, out=None, ws=None, stream=None):
     d, h, w = vol.shape
     if out is None:
         out = torch.empty((d, h, w), dtype=torch.int32, device=vol.device)
-    elif out.dtype != torch.int32 or tuple(out.shape) != (d, h, w) or not out.is_contiguous():
-        raise TypeError("out must be a contiguous int32 tensor shaped like vol")
+    else:
+        _check_out(out, (d, h, w), vol.device)
     need = ccl_workspace_bytes3d(d, h, w, conn)
     if need == 0:
         raise CclError(1, "ccl_workspace_bytes3d")
     if ws is None:
         ws = _workspace(need, vol.device)
+    else:
+        _check_ws(ws, vol.device)
     with torch.cuda.device(vol.device):
         st = load().ccl_label3d(vol.data_ptr(), out.data_ptr(), d, h, w, conn, ws.data_ptr(),
                                 ws.numel(), _stream_handle(stream))
@@ -209,6 +240,8 @@ def ccl_label_static(img, conn: int = 8, out=None, stream=None):
     h, w = img.shape
     if out is None:
         out = torch.empty((h, w), dtype=torch.int32, device=img.device)
+    else:
+        _check_out(out, (h, w), img.device)
     with torch.cuda.device(img.device):
         st = load().ccl_label_static(img.data_ptr(), out.data_ptr(), h, w, conn,
                                      _stream_handle(stream))
@@ -246,14 +279,23 @@ def ccl_label_batched(imgs: Sequence, conn: int = 8, outs: Optional[Sequence] = 
     for im in imgs:
         _check_img(im)
     dev = imgs[0].device
+    for im in imgs:
+        if im.device != dev:
+            raise TypeError("every image of a batch must be on the same device")
     if outs is None:
         outs = [torch.empty(tuple(im.shape), dtype=torch.int32, device=im.device) for im in imgs]
+    if len(outs) != len(imgs):
+        raise ValueError("outs must hold one tensor per image")
+    for im, o in zip(imgs, outs):
+        _check_out(o, tuple(im.shape), dev, "each of outs")
     arr = _image_array(imgs, outs)
     need = int(load().ccl_batched_workspace_bytes(arr, len(imgs), conn))
     if need == 0:
         raise CclError(1, "ccl_batched_workspace_bytes")
     if ws is None:
         ws = _workspace(need, dev)
+    else:
+        _check_ws(ws, dev)
     with torch.cuda.device(dev):
         st = load().ccl_label_batched(arr, len(imgs), conn, ws.data_ptr(), ws.numel(),
                                       _stream_handle(stream))
@@ -308,6 +350,19 @@ def ccl_shutdown() -> None:
     check(load().ccl_shutdown(), "ccl_shutdown")
 
 
+def ccl_set_hop_budget(smem_hops: int = 0, global_hops: int = 0) -> None:
+    """Failure injection for tests: the union-find hop budgets of the 2-D
+    kernels (0 = default); a walk that runs out makes ccl_sync raise
+    CCL_ERR_TIMEOUT."""
+    check(load().ccl_set_hop_budget(smem_hops, global_hops), "ccl_set_hop_budget")
+
+
+def ccl_inject_alloc_failures(count: int) -> None:
+    """Failure injection for tests: the next ``count`` library-owned workspace
+    allocations fail with CCL_ERR_OOM (0 clears them)."""
+    check(load().ccl_inject_alloc_failures(count), "ccl_inject_alloc_failures")
+
+
 def ccl_stats_workspace_bytes(height: int, width: int, max_comps: int) -> int:
     return int(load().ccl_stats_workspace_bytes(height, width, max_comps))
 
@@ -326,10 +381,19 @@ def ccl_component_stats(labels, max_comps: int, comps=None, ncomps=None, ws=None
     if comps is None:
         comps = torch.empty((max(max_comps, 1), COMPONENT_WORDS), dtype=torch.int32,
                             device=labels.device)
+    elif (not isinstance(comps, torch.Tensor) or not comps.is_cuda or comps.device != labels.device
+          or comps.dtype != torch.int32 or comps.dim() != 2 or comps.shape[1] != COMPONENT_WORDS
+          or comps.shape[0] < max_comps or not comps.is_contiguous()):
+        raise TypeError(f"comps must be a contiguous int32 CUDA tensor (>= max_comps, "
+                        f"{COMPONENT_WORDS}) on {labels.device}")
     if ncomps is None:
         ncomps = torch.empty(1, dtype=torch.int32, device=labels.device)
+    else:
+        _check_out(ncomps, (1,), labels.device, "ncomps")
     if ws is None:
         ws = _workspace(ccl_stats_workspace_bytes(h, w, max_comps), labels.device)
+    else:
+        _check_ws(ws, labels.device)
     check(load().ccl_component_stats(labels.data_ptr(), h, w, comps.data_ptr(), max_comps,
                                      ncomps.data_ptr(), ws.data_ptr(), ws.numel(),
                                      _stream_handle(stream)), "ccl_component_stats")
@@ -418,6 +482,15 @@ class Server:
               "ccl_server_stats")
         return {"p50_ms": p50.value, "p99_ms": p99.value, "gpix_per_s": gp.value,
                 "completed": done.value, "rejected": rej.value}
+
+    def timing(self) -> dict:
+        """Mean per-batch host-to-device copy, labelling and device-to-host copy
+        times (ms, CUDA events) over the batches completed so far."""
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_uint64()
+        check(load().ccl_server_timing(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                       ctypes.byref(n)), "ccl_server_timing")
+        return {"h2d_ms": a.value, "label_ms": b.value, "d2h_ms": c.value, "batches": n.value}
 
     def close(self) -> None:
         if self._h:

@@ -73,6 +73,8 @@ _SIGS = {
     "ccl_autotune": (_c.c_int, [_c.c_int, _c.c_int, _P]),
     "ccl_set_phase_events": (None, [_c.POINTER(_P)]),
     "ccl_shutdown": (_c.c_int, []),
+    "ccl_set_hop_budget": (_c.c_int, [_c.c_int, _c.c_int]),
+    "ccl_inject_alloc_failures": (_c.c_int, [_c.c_int]),
     "ccl_batched_workspace_bytes": (_c.c_size_t, [_c.POINTER(ccl_image), _c.c_int, _c.c_int]),
     "ccl_label_batched": (_c.c_int, [_c.POINTER(ccl_image), _c.c_int, _c.c_int, _P, _c.c_size_t,
                                      _P]),
@@ -84,6 +86,8 @@ _SIGS = {
                                     _c.POINTER(_c.c_double), _c.POINTER(_c.c_uint64),
                                     _c.POINTER(_c.c_uint64)]),
     "ccl_server_destroy": (_c.c_int, [_P]),
+    "ccl_server_timing": (_c.c_int, [_P, _c.POINTER(_c.c_double), _c.POINTER(_c.c_double),
+                                     _c.POINTER(_c.c_double), _c.POINTER(_c.c_uint64)]),
 }
 
 

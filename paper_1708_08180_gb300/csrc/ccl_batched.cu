@@ -10,8 +10,16 @@
 // table.  Each call rewrites the staging buffer and replays the graph, so the
 // graph does not depend on the images or on the caller's workspace.  Two slots
 // per (device, stream) let the host prepare batch k+1 while batch k runs.
+//
+// A small first kernel writes, into the caller's workspace, the image of
+// every tile and of every seam chunk, so that a block that takes a work item
+// from a queue finds its image with one load.  The seam and link kernels are
+// launched with programmatic stream serialisation: their blocks become
+// resident as the previous kernel's blocks run out of work, and wait
+// (griddepcontrol.wait) before reading that kernel's results.
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <tuple>
 #include <vector>
@@ -35,28 +43,25 @@ struct BatchHeader {
     int merge_ctr;         // work-queue heads (zero in the staged copy)
     int seam_ctr;
     int link_ctr;
-    int pad[9];
+    int pad0;
+    int *tile_img;         // image of every tile (caller workspace, written by kb_maps)
+    int *chunk_img;        // image of every seam chunk
+    int pad[4];
 };
 static_assert(sizeof(BatchHeader) == 64, "header size");
 
 constexpr size_t kHdrBytes = 256;
 
-__device__ __forceinline__ int find_image_by_tile(const BatchImage *imgs, int n, int t) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (imgs[mid].tile_off <= t) lo = mid; else hi = mid - 1;
+// The image of every tile and seam chunk, one block per image (grid-stride).
+__global__ void __launch_bounds__(256) kb_maps(const BatchHeader *hdr, const BatchImage *imgs) {
+    const int n = hdr->n;
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const Geom &g = imgs[k].a.g;
+        const int t0 = imgs[k].tile_off, nt = g.tiles_x * g.tiles_y;
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) hdr->tile_img[t0 + i] = k;
+        const long long c0 = imgs[k].chunk_off, nc = (seam_items(g) + 255) / 256;
+        for (long long i = threadIdx.x; i < nc; i += blockDim.x) hdr->chunk_img[c0 + i] = k;
     }
-    return lo;
-}
-
-__device__ __forceinline__ int find_image_by_chunk(const BatchImage *imgs, int n, long long c) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (imgs[mid].chunk_off <= c) lo = mid; else hi = mid - 1;
-    }
-    return lo;
 }
 
 template <int HS>
@@ -64,12 +69,13 @@ __global__ void __launch_bounds__(kThreads, 6) kb_merge(BatchHeader *hdr, const 
                                                      int *err) {
     __shared__ SmemMerge sm;
     __shared__ int s_tile, s_img;
-    const int n = hdr->n, total = hdr->total_tiles;
+    const int total = hdr->total_tiles;
+    pdl_launch_dependents();   // the seam kernel may start (it waits before reading)
     for (;;) {
         if (threadIdx.x == 0) {
             const int t = atomicAdd(&hdr->merge_ctr, 1);
             s_tile = t;
-            s_img = t < total ? find_image_by_tile(imgs, n, t) : 0;
+            s_img = t < total ? __ldcg(hdr->tile_img + t) : 0;
         }
         __syncthreads();
         const int t = s_tile;
@@ -91,14 +97,14 @@ __global__ void __launch_bounds__(256, 4) kb_seams(BatchHeader *hdr, const Batch
     __shared__ SmemSeams sm;
     __shared__ long long s_chunk;
     __shared__ int s_img;
-    const int n = hdr->n;
     const long long total = hdr->total_chunks;
+    pdl_wait();                // the local merge is complete and visible
     pdl_launch_dependents();   // the link kernel may start (it waits before its walks)
     for (;;) {
         if (threadIdx.x == 0) {
             const long long c = atomicAdd(&hdr->seam_ctr, 1);
             s_chunk = c;
-            s_img = c < total ? find_image_by_chunk(imgs, n, c) : 0;
+            s_img = c < total ? __ldcg(hdr->chunk_img + c) : 0;
         }
         __syncthreads();
         const long long c = s_chunk;
@@ -114,12 +120,12 @@ __global__ void __launch_bounds__(kThreads, 8) kb_link(BatchHeader *hdr, const B
                                                     int *err) {
     __shared__ SmemLink sm;
     __shared__ int s_tile, s_img;
-    const int n = hdr->n, total = hdr->total_tiles;
+    const int total = hdr->total_tiles;
     for (;;) {
         if (threadIdx.x == 0) {
             const int t = atomicAdd(&hdr->link_ctr, 1);
             s_tile = t;
-            s_img = t < total ? find_image_by_tile(imgs, n, t) : 0;
+            s_img = t < total ? __ldcg(hdr->tile_img + t) : 0;
         }
         __syncthreads();
         const int t = s_tile;
@@ -143,7 +149,8 @@ namespace {
 
 struct Layout {
     size_t desc_bytes;      // descriptor table capacity (header + entries)
-    size_t total_bytes;     // caller workspace: per-image scratch
+    size_t total_bytes;     // caller workspace: per-image scratch, then the maps
+    size_t maps_off;        // tile map (total_tiles ints), then chunk map
     std::vector<size_t> img_off;   // per image workspace offset (bits, then tiles)
     std::vector<Geom> geom;
     int total_tiles;
@@ -182,9 +189,11 @@ bool plan(const ccl_image *imgs, int n, int conn, Layout &L) {
         tiles += (long long)g.tiles_x * g.tiles_y;
         chunks += (seam_items(g) + 255) / 256;
     }
-    if (tiles > 0x7FFFFFFFLL) return false;
+    if (tiles > 0x7FFFFFFFLL || chunks > 0x7FFFFFFFLL) return false;
     L.total_tiles = (int)tiles;
     L.total_chunks = chunks;
+    L.maps_off = off;
+    off += align256((size_t)tiles * 4u) + align256((size_t)chunks * 4u);
     L.total_bytes = off;
     return true;
 }
@@ -202,7 +211,11 @@ struct GraphSlot {
     int exec_conn = 0;
 };
 
+// Per (device, stream): its two slots and capture stream, under its own
+// mutex, so that a call waiting for its slot's previous batch does not hold
+// up calls on other streams (g_mu only guards the maps).
 struct StreamState {
+    std::mutex mu;
     GraphSlot slot[2];
     int next = 0;
     cudaStream_t capture = nullptr;
@@ -210,7 +223,7 @@ struct StreamState {
 
 std::mutex g_mu;
 std::map<int, Persist> g_persist;
-std::map<std::pair<int, cudaStream_t>, StreamState> g_state;
+std::map<std::pair<int, cudaStream_t>, std::shared_ptr<StreamState>> g_state;
 
 bool persist_dims(int dev, int conn, Persist &p) {
     auto it = g_persist.find(dev * 16 + conn);
@@ -236,13 +249,14 @@ bool persist_dims(int dev, int conn, Persist &p) {
 
 void launch_kernels(const Persist &p, int conn, BatchHeader *hdr, const BatchImage *imgs,
                     int *err, cudaStream_t s) {
+    kb_maps<<<p.link_blocks, 256, 0, s>>>(hdr, imgs);
     if (conn == 8) {
         kb_merge<2><<<p.merge_blocks, kThreads, 0, s>>>(hdr, imgs, err);
-        kb_seams<<<p.seam_blocks, 256, 0, s>>>(hdr, imgs, err);
+        launch_pdl(kb_seams, (unsigned)p.seam_blocks, 256u, s, hdr, imgs, err);
         launch_pdl(kb_link<2>, (unsigned)p.link_blocks, (unsigned)kThreads, s, hdr, imgs, err);
     } else {
         kb_merge<1><<<p.merge_blocks, kThreads, 0, s>>>(hdr, imgs, err);
-        kb_seams<<<p.seam_blocks, 256, 0, s>>>(hdr, imgs, err);
+        launch_pdl(kb_seams, (unsigned)p.seam_blocks, 256u, s, hdr, imgs, err);
         launch_pdl(kb_link<1>, (unsigned)p.link_blocks, (unsigned)kThreads, s, hdr, imgs, err);
     }
 }
@@ -260,11 +274,14 @@ void release_slot(GraphSlot &sl) {
 void free_batched_state() {
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto &kv : g_state) {
-        for (auto &sl : kv.second.slot) {
+        StreamState &ss = *kv.second;
+        std::lock_guard<std::mutex> lks(ss.mu);
+        for (auto &sl : ss.slot) {
             if (sl.done) cudaEventSynchronize(sl.done);
             release_slot(sl);
         }
-        if (kv.second.capture) cudaStreamDestroy(kv.second.capture);
+        if (ss.capture) cudaStreamDestroy(ss.capture);
+        ss.capture = nullptr;
     }
     g_state.clear();
     g_persist.clear();
@@ -287,10 +304,17 @@ static ccl_status enqueue_batched(const ccl_image *imgs, int n, int conn, void *
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CCL_ERR_CUDA;
 
-    std::lock_guard<std::mutex> lk(g_mu);
     Persist p;
-    if (!persist_dims(dev, conn, p)) return CCL_ERR_CUDA;
-    StreamState &ss = g_state[{dev, stream}];
+    std::shared_ptr<StreamState> ssp;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!persist_dims(dev, conn, p)) return CCL_ERR_CUDA;
+        auto &slot_ptr = g_state[{dev, stream}];
+        if (!slot_ptr) slot_ptr = std::make_shared<StreamState>();
+        ssp = slot_ptr;
+    }
+    StreamState &ss = *ssp;
+    std::lock_guard<std::mutex> lk(ss.mu);
     if (!ss.capture &&
         cudaStreamCreateWithFlags(&ss.capture, cudaStreamNonBlocking) != cudaSuccess)
         return CCL_ERR_CUDA;
@@ -321,6 +345,8 @@ static ccl_status enqueue_batched(const ccl_image *imgs, int n, int conn, void *
     h->n = n;
     h->total_tiles = L.total_tiles;
     h->total_chunks = L.total_chunks;
+    h->tile_img = reinterpret_cast<int *>(ws + L.maps_off);
+    h->chunk_img = reinterpret_cast<int *>(ws + L.maps_off + align256((size_t)L.total_tiles * 4u));
     BatchImage *hi = reinterpret_cast<BatchImage *>(static_cast<char *>(sl.staging) + kHdrBytes);
     int tiles = 0;
     long long chunks = 0;
@@ -337,6 +363,8 @@ static ccl_status enqueue_batched(const ccl_image *imgs, int n, int conn, void *
             (g.W % 4 == 0) && (reinterpret_cast<uintptr_t>(imgs[k].d_labels) % 16 == 0);
         b.a.level = -1;
         b.a.merge_out = 0;
+        b.a.hops_smem = hop_budget_smem();
+        b.a.hops_glob = hop_budget_glob();
         b.tile_off = tiles;
         b.chunk_off = chunks;
         tiles += g.tiles_x * g.tiles_y;

@@ -56,6 +56,8 @@ constexpr int kErrQueue = 64;
 // runs out the thread records an error and stops, so no input and no defect
 // can keep a kernel spinning.  Valid inputs stay far below both budgets
 // (chains are shortened by path halving / compression as they are walked).
+// The 2-D kernels take their budgets as arguments (these values unless a test
+// lowers them with ccl_set_hop_budget to make a walk run out on purpose).
 constexpr int kSmemHopBudget = 1 << 20;   // per thread per tile (shared memory)
 constexpr int kGlobHopBudget = 1 << 20;   // per thread per work item (global memory)
 

@@ -21,6 +21,10 @@ void *library_workspace(cudaStream_t stream, size_t bytes, ccl_status *st);
 // Release every library-owned workspace.
 void free_library_workspaces();
 
+// Hop budgets the 2-D kernels are launched with (ccl_set_hop_budget).
+int hop_budget_smem();
+int hop_budget_glob();
+
 // Argument checks shared by the entry points.
 bool valid_image_dims(int height, int width);
 inline bool valid_conn(int conn) { return conn == 4 || conn == 8; }

@@ -167,6 +167,8 @@ ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, in
     a.out_aligned16 = (width % 4 == 0) && (reinterpret_cast<uintptr_t>(d_labels) % 16 == 0);
     a.level = level;
     a.merge_out = merge_out ? 1 : 0;
+    a.hops_smem = hop_budget_smem();
+    a.hops_glob = hop_budget_glob();
     const bool local_only = (flags & CCL_FLAG_LOCAL_ONLY) != 0;
 
     const bool timed = t_phase_armed;

@@ -1,5 +1,6 @@
 // ccl_runtime.cu -- status strings, the device error word, library-owned
 // workspaces, ccl_sync / ccl_shutdown and host-only seam arithmetic.
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -13,6 +14,10 @@ namespace ccl {
 __device__ int g_ccl_error_word;
 
 namespace {
+// failure injection for tests (ccl_set_hop_budget, ccl_inject_alloc_failures)
+std::atomic<int> g_hops_smem{kSmemHopBudget};
+std::atomic<int> g_hops_glob{kGlobHopBudget};
+std::atomic<int> g_fail_allocs{0};
 std::mutex g_mu;
 std::map<int, int *> g_err_ptr;                                   // device -> address
 std::map<std::pair<int, cudaStream_t>, std::pair<void *, size_t>> g_ws;  // library workspaces
@@ -31,7 +36,19 @@ int *device_error_word() {
     return p;
 }
 
+int hop_budget_smem() { return g_hops_smem.load(std::memory_order_relaxed); }
+int hop_budget_glob() { return g_hops_glob.load(std::memory_order_relaxed); }
+
+// Consumes one injected allocation failure, if any is pending.
+static bool take_injected_failure() {
+    int c = g_fail_allocs.load();
+    while (c > 0 && !g_fail_allocs.compare_exchange_weak(c, c - 1)) {
+    }
+    return c > 0;
+}
+
 void *library_workspace(cudaStream_t stream, size_t bytes, ccl_status *st) {
+    if (take_injected_failure()) { *st = CCL_ERR_OOM; return nullptr; }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { *st = CCL_ERR_CUDA; return nullptr; }
     std::lock_guard<std::mutex> lk(g_mu);
@@ -106,6 +123,19 @@ extern "C" ccl_status ccl_sync(ccl_stream stream) {
             return CCL_ERR_CUDA;
         return CCL_ERR_TIMEOUT;
     }
+    return CCL_OK;
+}
+
+extern "C" ccl_status ccl_set_hop_budget(int smem_hops, int global_hops) {
+    if (smem_hops < 0 || global_hops < 0) return CCL_ERR_INVALID_ARG;
+    ccl::g_hops_smem.store(smem_hops ? smem_hops : ccl::kSmemHopBudget);
+    ccl::g_hops_glob.store(global_hops ? global_hops : ccl::kGlobHopBudget);
+    return CCL_OK;
+}
+
+extern "C" ccl_status ccl_inject_alloc_failures(int count) {
+    if (count < 0) return CCL_ERR_INVALID_ARG;
+    ccl::g_fail_allocs.store(count);
     return CCL_OK;
 }
 

@@ -12,7 +12,15 @@
 //
 // Admission: a request's footprint is its image (1 B/px) + labels (4 B/px) +
 // labelling scratch; a request whose footprint exceeds the whole budget is
-// rejected at submit, others wait until the budget has room.
+// rejected at submit, others wait until the budget has room.  Batch formation
+// takes queued requests in FIFO order and may look past one that does not fit
+// the free budget (at most kLookAhead queue entries), so a large request does
+// not hold back smaller ones behind it; a request passed over kMaxPassOvers
+// times stops the look-ahead until it is admitted, so it cannot starve.
+//
+// Timing: each batch records CUDA events around its host-to-device copies,
+// its labelling launch and its device-to-host copies; ccl_server_timing
+// reports their mean durations per batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,7 +39,11 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+constexpr int kLookAhead = 32;      // queue entries examined past one that does not fit
+constexpr int kMaxPassOvers = 8;    // then strict FIFO until that request is admitted
+
 struct Request {
+    int passed_over = 0;            // batches formed while it waited at or near the head
     uint64_t id = 0;
     const uint8_t *h_img = nullptr;
     int32_t *h_out = nullptr;
@@ -59,6 +71,8 @@ struct ccl_server {
     bool stopping = false;
     std::vector<std::thread> workers;
     // statistics
+    double t_h2d_ms = 0.0, t_label_ms = 0.0, t_d2h_ms = 0.0;
+    uint64_t timed_batches = 0;
     std::vector<double> lat_ms;
     uint64_t completed = 0, rejected = 0;
     double pixels = 0.0;
@@ -66,7 +80,8 @@ struct ccl_server {
     Clock::time_point t_first, t_last;
 
     void worker_main(int slot);
-    ccl_status run_batch(cudaStream_t s, std::vector<Request *> &batch);
+    ccl_status run_batch(cudaStream_t s, cudaEvent_t *ev, std::vector<Request *> &batch);
+    bool take_batch(std::vector<Request *> &batch, size_t &bytes);
 };
 
 static size_t request_footprint(int h, int w, int conn) {
@@ -75,7 +90,7 @@ static size_t request_footprint(int h, int w, int conn) {
     return align256(px) + align256(px * 4) + ccl_batched_workspace_bytes(&im, 1, conn);
 }
 
-ccl_status ccl_server::run_batch(cudaStream_t s, std::vector<Request *> &batch) {
+ccl_status ccl_server::run_batch(cudaStream_t s, cudaEvent_t *ev, std::vector<Request *> &batch) {
     const int n = (int)batch.size();
     std::vector<ccl_image> ims(n);
     std::vector<size_t> img_off(n), lab_off(n);
@@ -102,6 +117,7 @@ ccl_status ccl_server::run_batch(cudaStream_t s, std::vector<Request *> &batch) 
     }
     char *base = static_cast<char *>(arena);
     ccl_status st = CCL_OK;
+    if (ev) cudaEventRecord(ev[0], s);
     for (int k = 0; k < n && st == CCL_OK; ++k) {
         const size_t px = (size_t)batch[k]->h * batch[k]->w;
         ims[k].d_img = reinterpret_cast<const uint8_t *>(base + img_off[k]);
@@ -110,20 +126,63 @@ ccl_status ccl_server::run_batch(cudaStream_t s, std::vector<Request *> &batch) 
             cudaSuccess)
             st = CCL_ERR_CUDA;
     }
+    if (ev) cudaEventRecord(ev[1], s);
     if (st == CCL_OK)
         st = ccl_label_batched(ims.data(), n, cfg.connectivity, base + ws_off, ws_bytes, s);
+    if (ev) cudaEventRecord(ev[2], s);
     for (int k = 0; k < n && st == CCL_OK; ++k) {
         const size_t px = (size_t)batch[k]->h * batch[k]->w;
         if (cudaMemcpyAsync(batch[k]->h_out, ims[k].d_labels, px * 4, cudaMemcpyDeviceToHost, s) !=
             cudaSuccess)
             st = CCL_ERR_CUDA;
     }
+    if (ev) cudaEventRecord(ev[3], s);
     cudaFreeAsync(arena, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         st = CCL_ERR_CUDA;
     }
+    if (ev && st == CCL_OK) {
+        float a = 0.f, b = 0.f, c = 0.f;
+        if (cudaEventElapsedTime(&a, ev[0], ev[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&b, ev[1], ev[2]) == cudaSuccess &&
+            cudaEventElapsedTime(&c, ev[2], ev[3]) == cudaSuccess) {
+            std::lock_guard<std::mutex> lk(mu);
+            t_h2d_ms += a;
+            t_label_ms += b;
+            t_d2h_ms += c;
+            ++timed_batches;
+        } else {
+            cudaGetLastError();
+        }
+    }
     return st;
+}
+
+// Called with mu held: move the next batch out of the queue.  FIFO among the
+// requests that fit; the scan looks at most kLookAhead entries past the first
+// one that does not fit, and not past one that was passed over too often.
+bool ccl_server::take_batch(std::vector<Request *> &batch, size_t &bytes) {
+    int skipped = 0;
+    for (auto it = pending.begin(); it != pending.end() && (int)batch.size() < cfg.max_batch;) {
+        Request *r = *it;
+        if (in_use + bytes + r->footprint <= cfg.hbm_budget_bytes) {
+            batch.push_back(r);
+            bytes += r->footprint;
+            it = pending.erase(it);
+            continue;
+        }
+        if (r->passed_over >= kMaxPassOvers || ++skipped > kLookAhead) break;
+        ++it;
+    }
+    if (batch.empty()) return false;
+    // every request still queued ahead of an admitted one was passed over
+    const uint64_t last = batch.back()->id;
+    for (Request *r : pending) {
+        if (r->id > last) break;
+        ++r->passed_over;
+    }
+    return true;
 }
 
 void ccl_server::worker_main(int slot) {
@@ -131,30 +190,24 @@ void ccl_server::worker_main(int slot) {
     cudaSetDevice(cfg.device);
     cudaStream_t s = nullptr;
     const bool stream_ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    cudaEvent_t ev[4] = {};
+    bool ev_ok = stream_ok;
+    for (auto &e : ev)
+        if (ev_ok && cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); ev_ok = false; }
     for (;;) {
         std::vector<Request *> batch;
         size_t bytes = 0;
         {
             std::unique_lock<std::mutex> lk(mu);
             for (;;) {
-                if (!pending.empty()) {
-                    while (!pending.empty() && (int)batch.size() < cfg.max_batch) {
-                        Request *r = pending.front();
-                        if (in_use + bytes + r->footprint > cfg.hbm_budget_bytes) break;
-                        batch.push_back(r);
-                        bytes += r->footprint;
-                        pending.pop_front();
-                    }
-                    if (!batch.empty()) break;
-                } else if (stopping) {
-                    break;
-                }
+                if (!pending.empty() && take_batch(batch, bytes)) break;
+                if (pending.empty() && stopping) break;
                 cv_work.wait(lk);
             }
             if (batch.empty()) break;   // stopping and nothing left
             in_use += bytes;
         }
-        const ccl_status st = stream_ok ? run_batch(s, batch) : CCL_ERR_CUDA;
+        const ccl_status st = stream_ok ? run_batch(s, ev_ok ? ev : nullptr, batch) : CCL_ERR_CUDA;
         const auto now = Clock::now();
         {
             std::lock_guard<std::mutex> lk(mu);
@@ -174,6 +227,8 @@ void ccl_server::worker_main(int slot) {
         cv_done.notify_all();
         cv_work.notify_all();
     }
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
     if (s) cudaStreamDestroy(s);
 }
 
@@ -294,6 +349,18 @@ extern "C" ccl_status ccl_server_stats(ccl_server *srv, double *p50_ms, double *
     }
     if (completed) *completed = srv->completed;
     if (rejected) *rejected = srv->rejected;
+    return CCL_OK;
+}
+
+extern "C" ccl_status ccl_server_timing(ccl_server *srv, double *h2d_ms, double *label_ms,
+                                        double *d2h_ms, uint64_t *batches) {
+    if (!srv) return CCL_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    const double n = srv->timed_batches ? (double)srv->timed_batches : 1.0;
+    if (h2d_ms) *h2d_ms = srv->t_h2d_ms / n;
+    if (label_ms) *label_ms = srv->t_label_ms / n;
+    if (d2h_ms) *d2h_ms = srv->t_d2h_ms / n;
+    if (batches) *batches = srv->timed_batches;
     return CCL_OK;
 }
 

@@ -18,6 +18,8 @@ struct ImageArgs {
     int out_aligned16;     // label rows start on 16-byte boundaries (W % 4 == 0)
     int level;             // -1: foreground = nonzero byte; else byte == level
     int merge_out;         // link writes only its foreground pixels, keeping the others
+    int hops_smem;         // hop budget of each shared-memory walk sequence (per thread, tile)
+    int hops_glob;         // hop budget of each global-forest walk sequence (per thread, item)
 };
 
 // Shared memory of the local-merge phase.
@@ -154,7 +156,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     // larger-key root under the smaller; (4) the few that lose a race run as
     // lock-free unions with finds.  (5) Pointer jumping points every node
     // straight at its root.
-    int budget = kSmemHopBudget;
+    int budget = a.hops_smem;
     if (s > 0) {
         const int up = tid - NW;
         const uint32_t av = sm.bot[up];
@@ -293,8 +295,24 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     // ---- roots that reach a seam with a neighbouring tile ----
     // Each record position (top/bottom row per column, left/right column per
     // strip) remembers its segment's root; roots of positions that can touch
-    // a neighbour are flagged.
-    auto mark = [&](int r) { atomicOr(&sm.flag[r >> 5], 1u << (r & 31)); };
+    // a neighbour are flagged and given a border slot.
+    // The first thread to flag a root gives it a border slot and makes it a
+    // root node of the global forest (K then holds the slot), so no pass over
+    // all nodes is needed to find the flagged roots.
+    gnode *par = reinterpret_cast<gnode *>(tw_ + g.off_par);
+    auto mark = [&](int r) {
+        const uint32_t bit = 1u << (r & 31);
+        if (atomicOr(&sm.flag[r >> 5], bit) & bit) return;   // flagged already
+        const int j = atomicAdd(&sm.nborder, 1);
+        if (j < g.border_cap) {
+            const int gk = gkey(sm.K[r]);
+            st_policy(tw_ + g.off_key + j, gk, l2_evict_last());
+            st_policy(par + j, make_gnode(gk, tile, j), l2_evict_last());
+            sm.K[r] = (uint16_t)j;
+        } else {
+            atomicOr(err, kErrBorderCap);
+        }
+    };
     int r_top = -1, r_bot = -1, r_left = -1, r_right = -1;
     if (tid < TW) {
         const int wc = tid >> 5, b = tid & 31;
@@ -331,25 +349,6 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     }
     __syncthreads();
     auto flagged = [&](int r) { return (sm.flag[r >> 5] >> (r & 31)) & 1u; };
-
-    // ---- border roots: a slot each, and a root node of the global forest ----
-    if (!local_only) {
-        gnode *par = reinterpret_cast<gnode *>(tw_ + g.off_par);
-        for (int n = tid; n < total; n += kThreads) {
-            if (sm.P[n] == n && flagged(n)) {
-                const int j = atomicAdd(&sm.nborder, 1);
-                if (j < g.border_cap) {
-                    const int gk = gkey(sm.K[n]);
-                    st_policy(tw_ + g.off_key + j, gk, l2_evict_last());
-                    st_policy(par + j, make_gnode(gk, tile, j), l2_evict_last());
-                    sm.K[n] = (uint16_t)j;
-                } else {
-                    atomicOr(err, kErrBorderCap);
-                }
-            }
-        }
-        __syncthreads();
-    }
 
     // ---- seam records: the global node of each position's root ----
     long long *rec64 = reinterpret_cast<long long *>(rec);
@@ -455,7 +454,7 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
     const Geom &g = a.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const GlobalForest F{a.tws, g.tile_ints, g.off_par};
-    int budget = kGlobHopBudget;
+    int budget = a.hops_glob;
     gnode(*list)[2] = sm.list[warp];
     int n = 0;   // warp-uniform list length
     const long long idx = idx0 + threadIdx.x;
@@ -707,7 +706,7 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
     {
         const GlobalForest F{a.tws, g.tile_ints, g.off_par};
         const gnode *par = reinterpret_cast<const gnode *>(tw_ + g.off_par);
-        int budget = kGlobHopBudget;
+        int budget = a.hops_glob;
         for (int j = tid; j < nb; j += kThreads) {
             gnode r = __ldcg(par + j);
             for (;;) {
@@ -768,17 +767,45 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
             __stcs(reinterpret_cast<int4 *>(out), make_int4(v[0], v[1], v[2], v[3]));
         }
     } else {
-        for (int id = tid; id < TH * TW; id += kThreads) {
-            const int r = id / TW, c = id % TW;
-            if (r >= nrows || c >= ncols) continue;
-            const int wq = c >> 5, b = c & 31;
-            const int o = (r / HS) * NW + wq;
-            const uint32_t rb = sm.rows[r * NW + wq];
-            const uint32_t sq = sm.st[o];
-            const int cur = sm.base[o] + __popc(sq & le_mask(b)) - 1;
-            int32_t *out = a.labels + (size_t)(y0 + r) * g.W + x0 + c;
-            if ((rb >> b) & 1u) *out = sm.S[cur < 0 ? 0 : cur];
-            else if (!a.merge_out) *out = 0;
+        // rows not 16-byte aligned (W % 4 != 0 or an unaligned label pointer):
+        // chunks of 4 labels at 16-byte aligned addresses, so that the inside
+        // of every row is written with 16-byte stores and only the chunks
+        // that overhang the row's ends with single ones.  The head of a row
+        // is the number of labels between its start and the 16-byte boundary
+        // below it; a chunk's 4 pixels may then straddle two bit words.
+        constexpr int CPR = TW / 4 + 1;
+        for (int id = tid; id < TH * CPR; id += kThreads) {
+            const int r = id / CPR, k = id % CPR;
+            if (r >= nrows) continue;
+            int32_t *row = a.labels + (size_t)(y0 + r) * g.W + x0;
+            const int head = (int)((reinterpret_cast<uintptr_t>(row) >> 2) & 3u);
+            const int c0 = 4 * k - head;   // tile column of the chunk's first label
+            if (c0 >= ncols) continue;
+            int v[4];
+            bool in[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = c0 + e;
+                in[e] = c >= 0 && c < ncols;
+                v[e] = 0;
+                if (in[e]) {
+                    const int wq = c >> 5, b = c & 31;
+                    const int o = (r / HS) * NW + wq;
+                    if ((sm.rows[r * NW + wq] >> b) & 1u) {
+                        const int cur = sm.base[o] + __popc(sm.st[o] & le_mask(b)) - 1;
+                        v[e] = sm.S[cur < 0 ? 0 : cur];
+                    } else if (a.merge_out) {
+                        v[e] = row[c];   // keep the pixels this pass does not label
+                    }
+                }
+            }
+            if (in[0] && in[3]) {
+                __stcs(reinterpret_cast<int4 *>(row + c0), make_int4(v[0], v[1], v[2], v[3]));
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (in[e]) row[c0 + e] = v[e];
+            }
         }
     }
 }

@@ -195,3 +195,34 @@ def test_binding_rejects_host_tensors_and_bad_shapes(lib):
                  lambda: ccl.ccl_label(img.float(), 8)):
         with pytest.raises(TypeError):
             call()
+
+
+def test_failure_injection_hooks_validate_and_fail_allocation_on_host(lib):
+    """An injected allocation failure makes a call that needs a library-owned
+    workspace return CCL_ERR_OOM before any CUDA call (so this runs without a
+    GPU); negative counts and budgets are refused."""
+    P = ctypes.c_void_p
+    assert lib.ccl_inject_alloc_failures(-1) == _lib.CCL_ERR_INVALID_ARG
+    assert lib.ccl_set_hop_budget(-1, 0) == _lib.CCL_ERR_INVALID_ARG
+    assert lib.ccl_set_hop_budget(0, -5) == _lib.CCL_ERR_INVALID_ARG
+    assert lib.ccl_set_hop_budget(0, 0) == _lib.CCL_OK
+    assert lib.ccl_inject_alloc_failures(2) == _lib.CCL_OK
+    try:
+        assert lib.ccl_label(P(256), P(512), 64, 64, 8, None, 0, None) == _lib.CCL_ERR_OOM
+        assert lib.ccl_label_tiled(P(256), P(512), 64, 64, 4, 32, 0, None, 0, None) == \
+            _lib.CCL_ERR_OOM
+    finally:
+        assert lib.ccl_inject_alloc_failures(0) == _lib.CCL_OK
+
+
+def test_binding_rejects_bad_workspace_and_outputs_without_gpu(lib):
+    """Host-memory images are refused before any output or workspace check."""
+    import torch
+
+    img = torch.zeros((8, 8), dtype=torch.uint8)
+    with pytest.raises(TypeError):
+        ccl.ccl_label_static(img, 8)
+    with pytest.raises(TypeError):
+        ccl.ccl_label_batched([img], 8)
+    with pytest.raises(TypeError):
+        ccl.ccl_component_stats(torch.zeros((8, 8), dtype=torch.int32), 4)

@@ -141,21 +141,62 @@ def test_repeat_runs_identical(conn):
 @pytest.mark.parametrize("n", [1024, 2048])
 @pytest.mark.parametrize("conn", [4, 8])
 def test_density_sweep_full_range(n, conn):
-    """Densities 0.1 ... 0.9 in steps of 0.1, two seeds each, at 1024^2 and
-    2048^2 (the sweep of the plain-path workload at sizes the oracle labels
-    in a fraction of a second)."""
+    """The plain-path sweep at 1024^2 and 2048^2: densities 0.1 ... 0.9 in
+    steps of 0.1, seeds 0-9, every image compared in full with the oracle."""
     for k in range(1, 10):
         p = k / 10
-        for seed in (0, 1):
+        for seed in range(10):
             img = synthetic.bernoulli(n, n, p, seed)
             assert_same(gpu_label(img, conn), oracle.label(img, conn), f"{n} p={p} seed={seed}")
 
 
-@pytest.mark.parametrize("p", [0.1, 0.4, 0.5, 0.6, 0.9])
+@pytest.mark.parametrize("p", [k / 10 for k in range(1, 10)])
 @pytest.mark.parametrize("conn", [4, 8])
 def test_density_sweep_4096(p, conn):
-    img = synthetic.bernoulli(4096, 4096, p, 0)
-    assert_same(gpu_label(img, conn), oracle.label(img, conn), f"4096 p={p}")
+    """4096^2 at every density of the sweep; seeds 0-9 around the
+    site-percolation thresholds (p = 0.4, 0.5, 0.6: about 0.41 for
+    8-connectivity, 0.59 for 4-connectivity), where the components crossing
+    tile seams are largest, seed 0 elsewhere."""
+    seeds = range(10) if p in (0.4, 0.5, 0.6) else (0,)
+    for seed in seeds:
+        img = synthetic.bernoulli(4096, 4096, p, seed)
+        assert_same(gpu_label(img, conn), oracle.label(img, conn), f"4096 p={p} seed={seed}")
+
+
+@pytest.fixture(scope="module")
+def buffers_8192():
+    n = 8192
+    need = max(ccl.ccl_workspace_bytes(n, n, c) for c in (4, 8))
+    ws = torch.empty(need, dtype=torch.uint8, device=DEV)
+    out = torch.empty((n, n), dtype=torch.int32, device=DEV)
+    dimg = torch.empty((n, n), dtype=torch.uint8, device=DEV)
+    return dimg, out, ws
+
+
+@pytest.mark.parametrize("p", [k / 10 for k in range(1, 10)])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_density_sweep_8192(p, conn, buffers_8192):
+    """8192^2 at every density and both connectivities, in the launch
+    configuration bench.py times (ccl_label, default tile, caller workspace,
+    current stream), compared in full with the oracle.  Seeds 1 and 2 are
+    added at the densities next to the percolation thresholds (0.4 and 0.6),
+    where seam unions meet the longest chains in the global forest."""
+    dimg, out, ws = buffers_8192
+    seeds = (0, 1, 2) if p in (0.4, 0.6) else (0,)
+    for seed in seeds:
+        img = synthetic.bernoulli(8192, 8192, p, seed)
+        dimg.copy_(torch.from_numpy(img))
+        out.fill_(-3)
+        ccl.ccl_label(dimg, conn, out=out, ws=ws)
+        ccl.ccl_sync()
+        assert_same(out.cpu().numpy(), oracle.label(img, conn), f"8192 p={p} conn={conn} seed={seed}")
+
+
+def test_small_config_512_seeds():
+    """The 512^2 workload (Bernoulli 0.5, 8-connectivity), seeds 0-9."""
+    for seed in range(10):
+        img = synthetic.bernoulli(512, 512, 0.5, seed, cfg_id=synthetic.CFG_SMALL)
+        assert_same(gpu_label(img, 8), oracle.label(img, 8), f"512 seed={seed}")
 
 
 def test_full_size_headline_8192():
