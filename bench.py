@@ -602,6 +602,43 @@ def stats_leg(labels, stream, reps: int = 50):
             "what": "pixel count, bounding box and coordinate sums of every component"}
 
 
+def fused_stats_leg(imgs, outs, label_ms: float, stream, reps: int = 50):
+    """ccl_label_with_stats on the headline images (labels and every
+    component's statistics in one pass): device time per call (CUDA events,
+    inputs rotated as in the headline loop), against the labelling alone."""
+    import torch
+
+    import paper_1708_08180_gb300 as ccl
+
+    h, w = imgs[0].shape
+    dev = imgs[0].device
+    _, _, nc = ccl.ccl_label_with_stats(imgs[0], CONN, 0, out=outs[0], stream=stream)
+    torch.cuda.synchronize()
+    n = int(nc.item())
+    cap = n + n // 4 + 1024
+    comps = torch.empty((cap, ccl.COMPONENT_WORDS), dtype=torch.int32, device=dev)
+    ncomps = torch.empty(1, dtype=torch.int32, device=dev)
+    wss = [torch.empty(ccl.ccl_workspace_bytes_with_stats(h, w, CONN), dtype=torch.uint8,
+                       device=dev) for _ in imgs]
+    for k in range(3):
+        ccl.ccl_label_with_stats(imgs[k % len(imgs)], CONN, cap, out=outs[k % len(imgs)], comps=comps,
+                                 ncomps=ncomps, ws=wss[k % len(imgs)], stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(reps):
+        ccl.ccl_label_with_stats(imgs[k % len(imgs)], CONN, cap, out=outs[k % len(imgs)], comps=comps,
+                                 ncomps=ncomps, ws=wss[k % len(imgs)], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ccl.ccl_sync(stream)
+    ms = e0.elapsed_time(e1) / reps
+    return {"components": n, "ms": round(ms, 5), "gpix_s": round(h * w / (ms / 1e3) / 1e9, 2),
+            "ratio_to_labelling": round(ms / label_ms, 3), "gpu_launches_per_call": 4,
+            "what": "labels plus count, bounding box and coordinate sums of every component, "
+                    "gathered in the link pass (ccl_label_with_stats)"}
+
+
 def regions_leg(img, out, ws, stream, reps: int = 50):
     """ccl_label_regions on the headline image with levels {0, 1}: every
     region, background included (one three-phase pass per level).  Device
@@ -825,6 +862,7 @@ def run_ours(args, rank, world, local):
         line["structured_4096"] = structured_leg(dev, stream)
     if rank == 0 and not args.no_stats:
         line["component_stats"] = stats_leg(outs[0], stream)
+        line["label_with_stats"] = fused_stats_leg(imgs, outs, ms_per_step, stream)
     if rank == 0 and not args.no_volume:
         line["volume"] = volume_leg(dev, stream, side=args.volume_side)
     if rank == 0 and not args.no_regions:

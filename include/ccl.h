@@ -292,6 +292,35 @@ ccl_status ccl_component_stats(const int32_t *d_labels, int height, int width,
                                ccl_component *d_comps, int max_comps, int32_t *d_ncomps,
                                void *d_ws, size_t ws_bytes, ccl_stream stream);
 
+/* Label one image and gather the statistics of every component in the same
+ * pass (the size and location of each region, §I): as ccl_label (same
+ * labels, arguments and errors), plus
+ *   d_comps   : device array of max_comps records (max_comps >= 0; may be NULL
+ *               when max_comps == 0).  Record order is unspecified; each holds
+ *               its component's label, so sorting by label gives the records
+ *               of ccl_component_stats.  When there are more components than
+ *               max_comps, max_comps of them (which ones is unspecified) are
+ *               written and nothing past the array.
+ *   d_ncomps  : device int32, receives the number of components (zeroed by
+ *               the call first).
+ *   d_ws      : workspace of ws_bytes >= ccl_workspace_bytes_with_stats(), or
+ *               NULL (library-owned).
+ * The local merge gives every component that stays inside a tile an output
+ * record; the link phase adds each segment's count, bounding box and
+ * coordinate sums (from its pixels' bits) into a per-tile table, and flushes
+ * it once per tile: into the record of a component inside the tile, or into
+ * an accumulator of the border root that is a crossing component's global
+ * root; a fourth kernel writes those components' records.  Enqueues four
+ * kernels and one memset on `stream`. */
+ccl_status ccl_label_with_stats(const uint8_t *d_img, int32_t *d_labels, int height, int width,
+                                int connectivity, ccl_component *d_comps, int max_comps,
+                                int32_t *d_ncomps, void *d_ws, size_t ws_bytes, ccl_stream stream);
+
+/* Workspace bytes of ccl_label_with_stats (the labelling workspace, each
+ * segment's component slot and the border-root accumulators), over every tile
+ * width; 0 on invalid arguments. */
+size_t ccl_workspace_bytes_with_stats(int height, int width, int connectivity);
+
 /* ------------------------------------------------------------------------ */
 /* Batched: many images of different sizes in one launch sequence           */
 /* ------------------------------------------------------------------------ */

@@ -27,7 +27,8 @@ __all__ = [
     "ccl_get_tile_table", "ccl_set_tile_table", "ccl_autotune", "load",
     "ccl_stats_workspace_bytes", "ccl_component_stats", "component_stats", "COMPONENT_FIELDS",
     "ccl_label_regions", "label_regions", "ccl_label3d", "ccl_workspace_bytes3d", "label3d",
-    "ccl_set_hop_budget", "ccl_inject_alloc_failures",
+    "ccl_set_hop_budget", "ccl_inject_alloc_failures", "ccl_label_with_stats",
+    "ccl_workspace_bytes_with_stats", "label_with_stats",
 ]
 
 # ccl_component as int32 words: label, count, xmin, ymin, xmax, ymax, then the
@@ -409,12 +410,83 @@ def component_stats(labels) -> dict:
     n = int(ncomps.item())
     comps, ncomps = ccl_component_stats(labels, n)     # then the records
     ccl_sync()
-    raw = comps[:n].cpu().numpy()
+    return _records_to_dict(comps.cpu().numpy(), n)
+
+
+def ccl_workspace_bytes_with_stats(height: int, width: int, conn: int) -> int:
+    return int(load().ccl_workspace_bytes_with_stats(height, width, conn))
+
+
+def ccl_label_with_stats(img, conn: int = 8, max_comps: int = 0, out=None, comps=None, ncomps=None,
+                         ws=None, stream=None):
+    """Label ``img`` and gather every component's statistics in the same pass.
+    ``comps``: CUDA int32 tensor (>= max_comps, 10) receiving records
+    (COMPONENT_FIELDS, sums as int64 word pairs) in unspecified order;
+    ``ncomps``: CUDA int32 tensor (1,) receiving the component count.  Returns
+    (out, comps, ncomps); tensors not given are allocated here."""
+    torch = _torch()
+    _check_img(img)
+    h, w = img.shape
+    if out is None:
+        out = torch.empty((h, w), dtype=torch.int32, device=img.device)
+    else:
+        _check_out(out, (h, w), img.device)
+    if comps is None:
+        comps = torch.empty((max(max_comps, 1), COMPONENT_WORDS), dtype=torch.int32,
+                            device=img.device)
+    elif (not isinstance(comps, torch.Tensor) or not comps.is_cuda or comps.device != img.device
+          or comps.dtype != torch.int32 or comps.dim() != 2 or comps.shape[1] != COMPONENT_WORDS
+          or comps.shape[0] < max_comps or not comps.is_contiguous()):
+        raise TypeError(f"comps must be a contiguous int32 CUDA tensor (>= max_comps, "
+                        f"{COMPONENT_WORDS}) on {img.device}")
+    if ncomps is None:
+        ncomps = torch.empty(1, dtype=torch.int32, device=img.device)
+    else:
+        _check_out(ncomps, (1,), img.device, "ncomps")
+    need = ccl_workspace_bytes_with_stats(h, w, conn)
+    if need == 0:
+        raise CclError(1, "ccl_workspace_bytes_with_stats")
+    if ws is None:
+        ws = _workspace(need, img.device)
+    else:
+        _check_ws(ws, img.device)
+    with torch.cuda.device(img.device):
+        st = load().ccl_label_with_stats(img.data_ptr(), out.data_ptr(), h, w, conn,
+                                         comps.data_ptr(), max_comps, ncomps.data_ptr(),
+                                         ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    check(st, "ccl_label_with_stats")
+    return out, comps, ncomps
+
+
+def _records_to_dict(raw, n: int) -> dict:
+    import numpy as np
+
+    raw = raw[:n]
     out = {f: raw[:, k].astype(np.int64) for k, f in enumerate(COMPONENT_FIELDS[:6])}
     wide = raw[:, 6:10].copy().view(np.int64)
     out["sum_x"] = wide[:, 0]
     out["sum_y"] = wide[:, 1]
     return out
+
+
+def label_with_stats(img, conn: int = 8):
+    """Labels and the statistics of every component, in one pass (blocking):
+    (labels, dict of CPU numpy arrays keyed by COMPONENT_FIELDS, in label
+    order).  The record capacity starts at one per 64 pixels and is raised to
+    the exact count if that is exceeded."""
+    import numpy as np
+
+    h, w = img.shape
+    cap = min(h * w // 2 + 2, h * w // 64 + 1024)
+    out, comps, ncomps = ccl_label_with_stats(img, conn, cap)
+    ccl_sync()
+    n = int(ncomps.item())
+    if n > cap:
+        out, comps, ncomps = ccl_label_with_stats(img, conn, n, out=out)
+        ccl_sync()
+    st = _records_to_dict(comps.cpu().numpy(), n)
+    order = np.argsort(st["label"], kind="stable")
+    return out, {k: v[order] for k, v in st.items()}
 
 
 def label(img, conn: int = 8, tile_w: int = 0):

@@ -66,6 +66,9 @@ _SIGS = {
     "ccl_stats_workspace_bytes": (_c.c_size_t, [_c.c_int, _c.c_int, _c.c_int]),
     "ccl_component_stats": (_c.c_int, [_P, _c.c_int, _c.c_int, _P, _c.c_int, _P, _P, _c.c_size_t,
                                        _P]),
+    "ccl_label_with_stats": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_int, _P, _c.c_int, _P, _P,
+                                        _c.c_size_t, _P]),
+    "ccl_workspace_bytes_with_stats": (_c.c_size_t, [_c.c_int, _c.c_int, _c.c_int]),
     "ccl_seam_pair_count": (_c.c_longlong, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int]),
     "ccl_sync": (_c.c_int, [_P]),
     "ccl_get_tile_table": (_c.c_int, [_c.c_int, _c.POINTER(_c.c_int)]),

@@ -41,6 +41,22 @@ void set_tile_table_entry(int conn, int hc, int wc, int tile_w);
 // griddepcontrol.launch_dependents (or exited); it must griddepcontrol.wait
 // before reading that grid's results.
 template <typename... P, typename... A>
+inline cudaError_t launch_pdl_smem(void (*kernel)(P...), unsigned grid, unsigned block,
+                                   size_t smem, cudaStream_t s, A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
+template <typename... P, typename... A>
 inline cudaError_t launch_pdl(void (*kernel)(P...), unsigned grid, unsigned block, cudaStream_t s,
                               A &&...args) {
     cudaLaunchConfig_t cfg = {};
@@ -59,11 +75,20 @@ inline cudaError_t launch_pdl(void (*kernel)(P...), unsigned grid, unsigned bloc
 // Release batched-path state.
 void free_batched_state();
 
+// Component-statistics outputs of ccl_label_with_stats.
+struct StatsOut {
+    void *comps;     // ccl_component records
+    int max_comps;
+    int32_t *ncomps;
+};
+
 // Enqueue the three single-image kernels with the given workspace (ccl_plain.cu).
 // level < 0: foreground = nonzero byte, else byte == level; merge_out: the
-// link phase writes only this pass's foreground pixels.
+// link phase writes only this pass's foreground pixels; so: also gather the
+// statistics of every component (a fourth kernel packs the border ones).
 ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, int width,
                          int conn, int tile_w, unsigned flags, void *d_ws, size_t ws_bytes,
-                         cudaStream_t stream, int level = -1, bool merge_out = false);
+                         cudaStream_t stream, int level = -1, bool merge_out = false,
+                         const StatsOut *so = nullptr);
 
 }  // namespace ccl

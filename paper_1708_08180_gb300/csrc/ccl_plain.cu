@@ -38,12 +38,12 @@ static int sm_count() {
 // several waves the local merge itself is launched that way, so that its
 // blocks are resident when the previous grid on the stream ends; they wait
 // for that grid (pdl_wait) before reading anything.
-template <int NW, int HS>
+template <int NW, int HS, bool STATS>
 __global__ void __launch_bounds__(kThreads) k_merge(ImageArgs a, int local_only, int *err) {
     __shared__ SmemMerge sm;
     pdl_wait();
     pdl_launch_dependents();
-    merge_tile<NW, HS>(a, blockIdx.x, local_only != 0, sm, err);
+    merge_tile<NW, HS, STATS>(a, blockIdx.x, local_only != 0, sm, err);
 }
 
 __global__ void __launch_bounds__(256, 4) k_seams(ImageArgs a, long long nitems, int *err) {
@@ -61,27 +61,98 @@ __global__ void __launch_bounds__(kThreads, 8) k_link(ImageArgs a, int *err) {
     link_tile<NW, HS>(a, blockIdx.x, sm, err);
 }
 
+// The link phase with component statistics (ccl_label_with_stats): the link
+// kernel's shared memory plus the per-tile statistics tables, dynamic.
+constexpr size_t kLinkStatsSmem = ((sizeof(SmemLink) + 15) & ~(size_t)15) + sizeof(SmemLinkStats);
+
+template <int NW, int HS>
+__global__ void __launch_bounds__(kThreads) k_link_stats(ImageArgs a, int *err) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    SmemLink &sm = *reinterpret_cast<SmemLink *>(dsm);
+    SmemLinkStats *sx = reinterpret_cast<SmemLinkStats *>(dsm + ((sizeof(SmemLink) + 15) & ~(size_t)15));
+    pdl_launch_dependents();
+    link_tile<NW, HS, true>(a, blockIdx.x, sm, err, sx);
+}
+
+// Statistics, last step: every border root that is its component's global
+// root emits the component's record from its accumulator (one slot range per
+// 256 border roots of a tile, reserved with one atomic).
+__global__ void __launch_bounds__(256) k_stats_pack(ImageArgs a, int *err) {
+    __shared__ int warp_sums[kThreads / 32];
+    __shared__ int s_base;
+    const Geom &g = a.g;
+    const int tile = blockIdx.x;
+    const int *tw_ = a.tws + (size_t)tile * g.tile_ints;
+    const int nb = min(__ldcg(tw_), g.border_cap);
+    const gnode *par = reinterpret_cast<const gnode *>(tw_ + g.off_par);
+    const BorderAcc *acc = static_cast<const BorderAcc *>(a.bacc) + (size_t)tile * g.border_cap;
+    CompRec *recs = static_cast<CompRec *>(a.comps);
+    for (int j0 = 0; j0 < nb; j0 += kThreads) {   // block-uniform trip count
+        const int j = j0 + (int)threadIdx.x;
+        int key = 0;
+        bool root = false;
+        if (j < nb) {
+            key = __ldcg(tw_ + g.off_key + j);
+            root = __ldcg(par + j) == make_gnode(key, tile, j);
+        }
+        int tot;
+        const int rank = block_excl_scan(root ? 1 : 0, warp_sums, tot);
+        if (threadIdx.x == 0) s_base = tot ? atomicAdd(a.ncomps, tot) : 0;
+        __syncthreads();
+        const long long o = (long long)s_base + rank;
+        if (root && o < a.max_comps) {
+            const BorderAcc &b = acc[j];
+            CompRec c;
+            c.label = 1 + key;
+            c.count = (int)b.count;
+            c.xmin = b.xmin;
+            c.ymin = b.ymin;
+            c.xmax = b.xmax;
+            c.ymax = b.ymax;
+            c.sum_x = (long long)b.sum_x;
+            c.sum_y = (long long)b.sum_y;
+            recs[o] = c;
+        }
+        __syncthreads();
+    }
+}
+
 // link_early: the link kernel directly follows the seam kernel and may start
 // early; otherwise (no seam kernel ran) it waits for the local merge as usual
 template <int NW, int HS>
 static void launch_merge_link(const ImageArgs &a, bool local_only, int *err, cudaStream_t s,
-                              bool link, bool link_early) {
+                              bool link, bool link_early, bool stats) {
     const int ntiles = a.g.tiles_x * a.g.tiles_y;
-    if (!link && ntiles > kMergeBlocksPerSm * sm_count())
-        launch_pdl(k_merge<NW, HS>, (unsigned)ntiles, (unsigned)kThreads, s, a, local_only ? 1 : 0, err);
-    else if (!link)
-        k_merge<NW, HS><<<ntiles, kThreads, 0, s>>>(a, local_only ? 1 : 0, err);
-    else if (link_early)
+    if (!link) {
+        void (*km)(ImageArgs, int, int *) = stats ? k_merge<NW, HS, true> : k_merge<NW, HS, false>;
+        if (ntiles > kMergeBlocksPerSm * sm_count())
+            launch_pdl(km, (unsigned)ntiles, (unsigned)kThreads, s, a, local_only ? 1 : 0, err);
+        else
+            km<<<ntiles, kThreads, 0, s>>>(a, local_only ? 1 : 0, err);
+    } else if (stats) {
+        static bool attr_set = false;   // per template instance; idempotent
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_link_stats<NW, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kLinkStatsSmem);
+            attr_set = true;
+        }
+        if (link_early)
+            launch_pdl_smem(k_link_stats<NW, HS>, (unsigned)ntiles, (unsigned)kThreads,
+                            kLinkStatsSmem, s, a, err);
+        else
+            k_link_stats<NW, HS><<<ntiles, kThreads, kLinkStatsSmem, s>>>(a, err);
+    } else if (link_early) {
         launch_pdl(k_link<NW, HS>, (unsigned)ntiles, (unsigned)kThreads, s, a, err);
-    else
+    } else {
         k_link<NW, HS><<<ntiles, kThreads, 0, s>>>(a, err);
+    }
 }
 
 static void launch_tile_kernel(const ImageArgs &a, bool local_only, int *err, cudaStream_t s,
-                               bool link, bool link_early = false) {
+                               bool link, bool link_early = false, bool stats = false) {
     const int nw = a.g.nw, hs = a.g.hs;
 #define CCL_CASE(NW_, HS_) \
-    if (nw == NW_ && hs == HS_) { launch_merge_link<NW_, HS_>(a, local_only, err, s, link, link_early); return; }
+    if (nw == NW_ && hs == HS_) { launch_merge_link<NW_, HS_>(a, local_only, err, s, link, link_early, stats); return; }
     CCL_CASE(1, 1) CCL_CASE(2, 1) CCL_CASE(4, 1) CCL_CASE(8, 1)
     CCL_CASE(1, 2) CCL_CASE(2, 2) CCL_CASE(4, 2) CCL_CASE(8, 2)
 #undef CCL_CASE
@@ -133,9 +204,18 @@ void set_tile_table_entry(int conn, int hc, int wc, int tile_w) {
 static thread_local cudaEvent_t t_phase_events[4];
 static thread_local bool t_phase_armed = false;
 
+// workspace of the statistics mode past the labelling workspace: component
+// slots per segment, then border-root accumulators
+size_t stats_extra_bytes(const Geom &g) {
+    const size_t tiles = (size_t)g.tiles_x * (size_t)g.tiles_y;
+    const size_t cs = (tiles * (size_t)cslot_stride(g) * 2u + 255u) & ~(size_t)255u;
+    const size_t ba = (tiles * (size_t)g.border_cap * sizeof(BorderAcc) + 255u) & ~(size_t)255u;
+    return cs + ba;
+}
+
 ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, int width,
                          int conn, int tile_w, unsigned flags, void *d_ws, size_t ws_bytes,
-                         cudaStream_t stream, int level, bool merge_out) {
+                         cudaStream_t stream, int level, bool merge_out, const StatsOut *so) {
     if (!d_img || !d_labels || !valid_image_dims(height, width) || !valid_conn(conn))
         return CCL_ERR_INVALID_ARG;
     const bool default_tile = tile_w == 0;
@@ -146,8 +226,14 @@ ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, in
     if (!geom_fits(g)) return CCL_ERR_INVALID_ARG;
     // the documented contract: ccl_workspace_bytes() for the default tile
     // width (it does not depend on the current table), the exact need otherwise
-    const size_t need = default_tile ? ccl_workspace_bytes(height, width, conn)
-                                     : bits_bytes(g) + tiles_bytes(g);
+    size_t need = default_tile ? ccl_workspace_bytes(height, width, conn)
+                               : bits_bytes(g) + tiles_bytes(g);
+    if (so) {
+        if (!so->comps && so->max_comps > 0) return CCL_ERR_INVALID_ARG;
+        if (!so->ncomps || so->max_comps < 0 || (flags & CCL_FLAG_LOCAL_ONLY) || level >= 0)
+            return CCL_ERR_INVALID_ARG;
+        need = ccl_workspace_bytes_with_stats(height, width, conn);
+    }
     ccl_status st = CCL_OK;
     if (!d_ws) {
         d_ws = library_workspace(stream, need, &st);
@@ -169,12 +255,28 @@ ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, in
     a.merge_out = merge_out ? 1 : 0;
     a.hops_smem = hop_budget_smem();
     a.hops_glob = hop_budget_glob();
+    a.comps = nullptr;
+    a.ncomps = nullptr;
+    a.cslot = nullptr;
+    a.bacc = nullptr;
+    a.max_comps = 0;
+    if (so) {
+        char *x = static_cast<char *>(d_ws) + bits_bytes(g) + tiles_bytes(g);
+        x = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(x) + 255u) & ~(uintptr_t)255u);
+        a.cslot = reinterpret_cast<uint16_t *>(x);
+        const size_t tiles = (size_t)g.tiles_x * (size_t)g.tiles_y;
+        a.bacc = x + ((tiles * (size_t)cslot_stride(g) * 2u + 255u) & ~(size_t)255u);
+        a.comps = so->comps;
+        a.ncomps = so->ncomps;
+        a.max_comps = so->max_comps;
+        if (cudaMemsetAsync(so->ncomps, 0, sizeof(int), stream) != cudaSuccess) return CCL_ERR_CUDA;
+    }
     const bool local_only = (flags & CCL_FLAG_LOCAL_ONLY) != 0;
 
     const bool timed = t_phase_armed;
     t_phase_armed = false;
     if (timed) cudaEventRecord(t_phase_events[0], stream);
-    launch_tile_kernel(a, local_only, err, stream, false);
+    launch_tile_kernel(a, local_only, err, stream, false, false, so != nullptr);
     if (timed) cudaEventRecord(t_phase_events[1], stream);
     const long long items = seam_items(g);
     const bool seams = !local_only && items > 0;
@@ -186,7 +288,8 @@ ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, in
             k_seams<<<(unsigned)blocks, 256, 0, stream>>>(a, items, err);
     }
     if (timed) cudaEventRecord(t_phase_events[2], stream);
-    launch_tile_kernel(a, local_only, err, stream, true, seams);
+    launch_tile_kernel(a, local_only, err, stream, true, seams, so != nullptr);
+    if (so) k_stats_pack<<<(unsigned)(g.tiles_x * g.tiles_y), 256, 0, stream>>>(a, err);
     if (timed) cudaEventRecord(t_phase_events[3], stream);
     if (cudaGetLastError() != cudaSuccess) return CCL_ERR_CUDA;
     return CCL_OK;
@@ -225,6 +328,30 @@ extern "C" ccl_status ccl_label(const uint8_t *d_img, int32_t *d_labels, int hei
                                 ccl_stream stream) {
     return ccl::enqueue_label(d_img, d_labels, height, width, connectivity, 0, 0u, d_ws,
                               ws_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// The need over every tile width, as ccl_workspace_bytes.
+extern "C" size_t ccl_workspace_bytes_with_stats(int height, int width, int connectivity) {
+    if (!ccl::valid_image_dims(height, width) || !ccl::valid_conn(connectivity)) return 0;
+    size_t m = 0;
+    for (int tw = 32; tw <= 256; tw <<= 1) {
+        const ccl::Geom g = ccl::make_geom(height, width, connectivity, tw);
+        if (!ccl::geom_fits(g)) return 0;
+        const size_t b = ((ccl::bits_bytes(g) + ccl::tiles_bytes(g) + 255u) & ~(size_t)255u) +
+                         ccl::stats_extra_bytes(g);
+        if (b > m) m = b;
+    }
+    return m;
+}
+
+extern "C" ccl_status ccl_label_with_stats(const uint8_t *d_img, int32_t *d_labels, int height,
+                                           int width, int connectivity, ccl_component *d_comps,
+                                           int max_comps, int32_t *d_ncomps, void *d_ws,
+                                           size_t ws_bytes, ccl_stream stream) {
+    static_assert(sizeof(ccl_component) == sizeof(ccl::CompRec), "record layout");
+    const ccl::StatsOut so{d_comps, max_comps, d_ncomps};
+    return ccl::enqueue_label(d_img, d_labels, height, width, connectivity, 0, 0u, d_ws, ws_bytes,
+                              reinterpret_cast<cudaStream_t>(stream), -1, false, &so);
 }
 
 extern "C" ccl_status ccl_label_regions(const uint8_t *d_img, int32_t *d_labels, int height,

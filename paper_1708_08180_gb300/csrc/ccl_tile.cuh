@@ -20,7 +20,38 @@ struct ImageArgs {
     int merge_out;         // link writes only its foreground pixels, keeping the others
     int hops_smem;         // hop budget of each shared-memory walk sequence (per thread, tile)
     int hops_glob;         // hop budget of each global-forest walk sequence (per thread, item)
+    // component statistics (the STATS kernels of ccl_label_with_stats only)
+    void *comps;           // output records (CompRec), max_comps of them
+    int *ncomps;           // component count (zeroed before the local merge)
+    uint16_t *cslot;       // per tile, cslot_stride entries: each segment's component slot
+    void *bacc;            // per tile, border_cap BorderAcc: border-root accumulators
+    int max_comps;
 };
+
+// One component's record, laid out as ccl_component of the C ABI.
+struct CompRec {
+    int32_t label, count, xmin, ymin, xmax, ymax;
+    long long sum_x, sum_y;
+};
+
+// Statistics gathered for a border root's component across tiles (global
+// coordinates): kept by the border root that is the component's global root.
+struct BorderAcc {
+    unsigned count;
+    int xmin, ymin, xmax, ymax, pad;
+    unsigned long long sum_x, sum_y;
+};
+
+__device__ __forceinline__ void init_border_acc(BorderAcc *b) {
+    b->count = 0u;
+    b->xmin = 0x7FFFFFFF;
+    b->ymin = 0x7FFFFFFF;
+    b->xmax = -1;
+    b->ymax = -1;
+    b->pad = 0;
+    b->sum_x = 0ull;
+    b->sum_y = 0ull;
+}
 
 // Shared memory of the local-merge phase.
 struct SmemMerge {
@@ -36,6 +67,8 @@ struct SmemMerge {
     int warp_sums[kThreads / 32];
     int nborder;
     int nq;
+    int nlocal;                    // statistics: components inside the tile
+    int out_base;                  // statistics: their first output record
 };
 
 // Shared memory of the link phase.
@@ -47,6 +80,37 @@ struct SmemLink {
     int base[kThreads];           // rank of the word's first segment start
     int warp_sums[kThreads / 32];
 };
+
+// Statistics mode of the link phase: per-tile aggregates of the components
+// the tile's segments belong to (tile coordinates), flushed once per tile.
+constexpr int kStatLocal = 128;    // components inside the tile aggregated in shared memory
+constexpr int kStatBorder = 128;   // global roots (of border roots) aggregated in shared memory
+constexpr int kStatHash = 1024;    // global roots of a tile's border roots (hash table)
+struct SmemLinkStats {
+    __align__(16) uint16_t C[kNodeCap];       // component slot per segment node (cslot encoding)
+    gnode G[kBorderCapMax];                   // global root of each border root
+    gnode HK[kStatHash];                      // hash table: the distinct global roots ...
+    uint16_t HV[kStatHash];                   // ... and their aggregate index in the tile
+    uint16_t HJ[kBorderCapMax];               // each border root's hash entry
+    unsigned LA[kStatLocal][7];               // count, xmin, ymin, xmax, ymax, sum x, sum y
+    unsigned BA[kStatBorder][7];              // per global root
+    int nroots;                               // distinct global roots in the tile
+};
+
+// A segment's component slot, 16 bits: a component inside the tile (its
+// record index in the tile, < 2^15), or a border root (bit 15 set, border slot
+// in the low bits).
+constexpr uint16_t kSlotBorder = 0x8000u;
+
+// per-tile stride of the component-slot array, in 16-bit entries (16-byte
+// multiple for cp.async)
+__host__ __device__ inline int cslot_stride(const Geom &g) { return (g.node_cap + 7) & ~7; }
+
+// sum of the positions of the set bits of v
+__device__ __forceinline__ int bit_position_sum(uint32_t v) {
+    return __popc(v & 0xAAAAAAAAu) + 2 * __popc(v & 0xCCCCCCCCu) + 4 * __popc(v & 0xF0F0F0F0u) +
+           8 * __popc(v & 0xFF00FF00u) + 16 * __popc(v & 0xFFFF0000u);
+}
 
 // rank of the segment containing column bit x (x in [-1, 31]) of a word with
 // segment starts `st` whose first start has rank `base`
@@ -66,7 +130,7 @@ __device__ __forceinline__ int seg_rank(int base, uint32_t st, int x) {
 //              seam with a neighbouring tile (also initialised as a root in the
 //              global union-find array G = labels buffer);
 //   records    global root index per seam pixel column/strip (-1: empty).
-template <int NW, int HS>
+template <int NW, int HS, bool STATS = false>
 __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool local_only,
                                            SmemMerge &sm, int *err) {
     constexpr int NS = kThreads / NW;
@@ -308,6 +372,8 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             const int gk = gkey(sm.K[r]);
             st_policy(tw_ + g.off_key + j, gk, l2_evict_last());
             st_policy(par + j, make_gnode(gk, tile, j), l2_evict_last());
+            if (STATS)
+                init_border_acc(static_cast<BorderAcc *>(a.bacc) + (size_t)tile * g.border_cap + j);
             sm.K[r] = (uint16_t)j;
         } else {
             atomicOr(err, kErrBorderCap);
@@ -366,10 +432,51 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     }
 
     // ---- per-segment labels ----
-    for (int n = tid; n < total; n += kThreads) {
-        const int r = sm.P[n];
-        const int k = sm.K[r];
-        st_policy(tw_ + kHdrInts + n, flagged(r) ? -(1 + k) : 1 + gkey(k), l2_evict_last());
+    if (!STATS) {
+        for (int n = tid; n < total; n += kThreads) {
+            const int r = sm.P[n];
+            const int k = sm.K[r];
+            st_policy(tw_ + kHdrInts + n, flagged(r) ? -(1 + k) : 1 + gkey(k), l2_evict_last());
+        }
+    } else {
+        // Statistics: every component inside the tile gets an output record
+        // (a slot in a range reserved with one atomic per tile) holding its
+        // label; each segment also stores its component's slot, local (>= 0)
+        // or border (-(1 + border slot)), for the link phase.
+        uint16_t *lslot = reinterpret_cast<uint16_t *>(sm.Q);   // the union queue is dead here
+        if (tid == 0) sm.nlocal = 0;
+        __syncthreads();
+        for (int n = tid; n < total; n += kThreads)
+            if (sm.P[n] == n && !flagged(n)) lslot[n] = (uint16_t)atomicAdd(&sm.nlocal, 1);
+        __syncthreads();
+        if (tid == 0) sm.out_base = sm.nlocal ? atomicAdd(a.ncomps, sm.nlocal) : 0;
+        __syncthreads();
+        const int ob = sm.out_base;
+        CompRec *recs = static_cast<CompRec *>(a.comps);
+        uint16_t *cs = a.cslot + (size_t)tile * cslot_stride(g);
+        for (int n = tid; n < total; n += kThreads) {
+            const int r = sm.P[n];
+            const int k = sm.K[r];
+            const bool f = flagged(r) != 0u;
+            st_policy(tw_ + kHdrInts + n, f ? -(1 + k) : 1 + gkey(k), l2_evict_last());
+            cs[n] = f ? (uint16_t)(kSlotBorder | k) : lslot[r];
+            if (r == n && !f) {
+                const long long o = (long long)ob + lslot[n];
+                if (o < a.max_comps) {
+                    CompRec c;
+                    c.label = 1 + gkey(k);
+                    c.count = 0;
+                    c.xmin = c.ymin = 0x7FFFFFFF;
+                    c.xmax = c.ymax = -1;
+                    c.sum_x = c.sum_y = 0;
+                    recs[o] = c;
+                }
+            }
+        }
+        if (tid == 0) {
+            tw_[2] = ob;
+            tw_[3] = sm.nlocal;
+        }
     }
     if (tid == 0) {
         tw_[0] = local_only ? 0 : min(sm.nborder, g.border_cap);
@@ -662,8 +769,9 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
 // give every segment its final label (its local root's, or the resolved label
 // of its border root), and write one int32 per pixel.  The stores are laid
 // out so that 32 lanes write 128 consecutive pixels (512 bytes) of one row.
-template <int NW, int HS>
-__device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink &sm, int *err) {
+template <int NW, int HS, bool STATS = false>
+__device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink &sm, int *err,
+                                          SmemLinkStats *sx = nullptr) {
     constexpr int NS = kThreads / NW;
     constexpr int TW = 32 * NW;
     constexpr int TH = NS * HS;
@@ -691,6 +799,23 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
                      "l"(tw_ + kHdrInts + 4 * c) : "memory");
     }
+    if (STATS) {   // the segments' component slots, the same way
+        const uint16_t *cs = a.cslot + (size_t)tile * cslot_stride(g);
+        for (int c = tid; c < (nseg + 7) / 8; c += kThreads) {
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(&sx->C[8 * c]);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(cs + 8 * c)
+                         : "memory");
+        }
+        if (tid == 0) sx->nroots = 0;
+        for (int i = tid; i < kStatLocal + kStatBorder; i += kThreads) {
+            unsigned *e = i < kStatLocal ? sx->LA[i] : sx->BA[i - kStatLocal];
+            e[0] = 0u;
+            e[1] = e[2] = 0xFFFFFFFFu;
+            e[3] = e[4] = 0u;
+            e[5] = e[6] = 0u;
+        }
+        for (int i = tid; i < kStatHash; i += kThreads) sx->HK[i] = kNoNode;
+    }
     asm volatile("cp.async.commit_group;" ::: "memory");
 #pragma unroll
     for (int j = 0; j < HS; ++j) sm.rows[(s * HS + j) * NW + w] = rows[j];
@@ -716,12 +841,28 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
                 r = p;
             }
             sm.R[j] = 1 + gnode_key(r);
+            if (STATS) sx->G[j] = r;
         }
     }
     int total;
     const int base = block_excl_scan(__popc(st), sm.warp_sums, total);   // syncs: R visible
     sm.st[tid] = st;
     sm.base[tid] = base;
+    if (STATS) {
+        // border roots of this tile with the same global root share one
+        // aggregate: a hash table on the global root gives each distinct root
+        // an index, taken by the thread that inserts it
+        for (int j = tid; j < nb; j += kThreads) {
+            const gnode r = sx->G[j];
+            unsigned h = (unsigned)((r ^ (r >> 29)) * 0x9E3779B1u) & (kStatHash - 1);
+            for (int probe = 0; probe < kStatHash; ++probe, h = (h + 1) & (kStatHash - 1)) {
+                const gnode old = atomicCAS(&sx->HK[h], kNoNode, r);
+                if (old == kNoNode) { sx->HV[h] = (uint16_t)atomicAdd(&sx->nroots, 1); break; }
+                if (old == r) break;
+            }
+            sx->HJ[j] = (uint16_t)h;
+        }
+    }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();   // every thread's copies of S have landed
     if (total != nseg) { if (tid == 0) atomicOr(err, kErrBorderCap); }
@@ -738,6 +879,148 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
         }
     }
     __syncthreads();
+
+    if (STATS) {
+        // Statistics of every piece of a segment inside this thread's word (the
+        // segments starting here, and the part of one continuing from the word
+        // before), from its pixels' bits: count, bounding box, coordinate sums.
+        // Aggregated per component in shared memory (components beyond the
+        // shared tables go straight to their global records), then flushed:
+        // a component inside the tile writes its record, a border component
+        // adds into the accumulator of its global root.
+        const int ob = __ldcg(tw_ + 2), nloc = __ldcg(tw_ + 3);
+        CompRec *recs = static_cast<CompRec *>(a.comps);
+        BorderAcc *bacc = static_cast<BorderAcc *>(a.bacc);
+        auto root_acc = [&](gnode r) {
+            const long long rt = (long long)((r >> kSlotBits) & (kMaxTiles - 1));
+            return bacc + (size_t)rt * g.border_cap + (int)(r & ((1u << kSlotBits) - 1u));
+        };
+        // Pieces are taken one per lane per step (warp-uniform trip count);
+        // lanes whose pieces belong to the same component (a border root is
+        // replaced by its tile representative) combine their values with warp
+        // reductions, and one lane per component updates the aggregate.
+        const int rep_hi = kStatBorder;
+        const bool has_pre = mL && (m & 1u) && base >= 1;
+        const uint32_t pre = has_pre ? (m & ~(m + 1u)) : 0u;   // run continuing from the word before
+        const int npieces = __popc(st) + (has_pre ? 1 : 0);
+        const int trips = __reduce_max_sync(0xFFFFFFFFu, npieces);
+        uint32_t rem = st;
+        bool pre_left = has_pre;
+        int n_next = base;
+        const int lane = tid & 31;
+        for (int t = 0; t < trips; ++t) {
+            int n = -1;
+            uint32_t mask = 0u;
+            if (pre_left) {
+                n = base - 1;
+                mask = pre;
+                pre_left = false;
+            } else if (rem) {
+                const int i = __ffs(rem) - 1;
+                rem &= rem - 1;
+                const uint32_t z = ~m & (0xFFFFFFFFu << i);
+                const int end = z ? __ffs(z) - 1 : 32;
+                mask = __funnelshift_lc(0xFFFFFFFFu, 0u, (unsigned)end) & (0xFFFFFFFFu << i);
+                n = n_next++;
+                if (n >= total) n = -1;
+            }
+            const bool act = n >= 0;
+            const unsigned am = __ballot_sync(0xFFFFFFFFu, act);
+            if (!act) continue;
+            const uint32_t tt = rows[0] & mask, bb = HS == 2 ? (rows[HS - 1] & mask) : 0u;
+            const uint32_t any = tt | bb;
+            const int ct = __popc(tt), cb = __popc(bb), cnt = ct + cb;
+            const int xw = 32 * w, ys = s * HS;
+            unsigned sxl = (unsigned)(xw * cnt + bit_position_sum(tt) + bit_position_sum(bb));
+            unsigned syl = (unsigned)(ys * ct + (ys + 1) * cb);
+            unsigned xmn = (unsigned)(xw + __ffs(any) - 1), xmx = (unsigned)(xw + 31 - __clz(any));
+            unsigned ymn = ct ? ys : ys + 1, ymx = cb ? ys + 1 : ys;
+            unsigned ucnt = (unsigned)cnt;
+            // c >= 0: a component inside the tile; c < 0: -(1 + aggregate index)
+            // of a global root (the hash entry of its border root)
+            const unsigned cv = sx->C[n];
+            int c = (int)cv;
+            unsigned hslot = 0u;
+            if (cv & kSlotBorder) {
+                const int j = (int)(cv & (kSlotBorder - 1u));
+                hslot = sx->HJ[j < nb ? j : 0];
+                c = -1 - (int)sx->HV[hslot];
+            }
+            const unsigned gm = __match_any_sync(am, c);
+            ucnt = __reduce_add_sync(gm, ucnt);
+            sxl = __reduce_add_sync(gm, sxl);
+            syl = __reduce_add_sync(gm, syl);
+            xmn = __reduce_min_sync(gm, xmn);
+            ymn = __reduce_min_sync(gm, ymn);
+            xmx = __reduce_max_sync(gm, xmx);
+            ymx = __reduce_max_sync(gm, ymx);
+            if (lane != __ffs(gm) - 1) continue;
+            unsigned *e = nullptr;
+            if (c >= 0 && c < kStatLocal) e = sx->LA[c];
+            else if (c < 0 && -c - 1 < rep_hi) e = sx->BA[-c - 1];
+            if (e) {
+                atomicAdd(e + 0, ucnt);
+                atomicMin(e + 1, xmn);
+                atomicMin(e + 2, ymn);
+                atomicMax(e + 3, xmx);
+                atomicMax(e + 4, ymx);
+                atomicAdd(e + 5, sxl);
+                atomicAdd(e + 6, syl);
+            } else if (c >= 0) {   // a component inside the tile, past the shared table
+                if ((long long)ob + c < a.max_comps) {
+                    CompRec *rc = recs + ob + c;
+                    atomicAdd(&rc->count, (int)ucnt);
+                    atomicMin(&rc->xmin, x0 + (int)xmn);
+                    atomicMin(&rc->ymin, y0 + (int)ymn);
+                    atomicMax(&rc->xmax, x0 + (int)xmx);
+                    atomicMax(&rc->ymax, y0 + (int)ymx);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&rc->sum_x),
+                              (unsigned long long)sxl + (unsigned long long)x0 * ucnt);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&rc->sum_y),
+                              (unsigned long long)syl + (unsigned long long)y0 * ucnt);
+                }
+            } else {               // a global root past the shared table
+                {
+                    BorderAcc *tacc = root_acc(sx->HK[hslot]);
+                    atomicAdd(&tacc->count, ucnt);
+                    atomicMin(&tacc->xmin, x0 + (int)xmn);
+                    atomicMin(&tacc->ymin, y0 + (int)ymn);
+                    atomicMax(&tacc->xmax, x0 + (int)xmx);
+                    atomicMax(&tacc->ymax, y0 + (int)ymx);
+                    atomicAdd(&tacc->sum_x, (unsigned long long)sxl + (unsigned long long)x0 * ucnt);
+                    atomicAdd(&tacc->sum_y, (unsigned long long)syl + (unsigned long long)y0 * ucnt);
+                }
+            }
+        }
+        __syncthreads();
+        for (int l = tid; l < min(nloc, kStatLocal); l += kThreads) {
+            if ((long long)ob + l >= a.max_comps) continue;
+            const unsigned *e = sx->LA[l];
+            CompRec *rc = recs + ob + l;
+            const int cnt = (int)e[0];
+            rc->count = cnt;
+            rc->xmin = x0 + (int)e[1];
+            rc->ymin = y0 + (int)e[2];
+            rc->xmax = x0 + (int)e[3];
+            rc->ymax = y0 + (int)e[4];
+            rc->sum_x = (long long)e[5] + (long long)x0 * cnt;
+            rc->sum_y = (long long)e[6] + (long long)y0 * cnt;
+        }
+        for (int h = tid; h < kStatHash; h += kThreads) {
+            const gnode r = sx->HK[h];
+            if (r == kNoNode || sx->HV[h] >= kStatBorder) continue;
+            const unsigned *e = sx->BA[sx->HV[h]];
+            if (e[0] == 0u) continue;
+            BorderAcc *t = root_acc(r);
+            atomicAdd(&t->count, e[0]);
+            atomicMin(&t->xmin, x0 + (int)e[1]);
+            atomicMin(&t->ymin, y0 + (int)e[2]);
+            atomicMax(&t->xmax, x0 + (int)e[3]);
+            atomicMax(&t->ymax, y0 + (int)e[4]);
+            atomicAdd(&t->sum_x, (unsigned long long)e[5] + (unsigned long long)x0 * e[0]);
+            atomicAdd(&t->sum_y, (unsigned long long)e[6] + (unsigned long long)y0 * e[0]);
+        }
+    }
 
     const int ncols = min(TW, g.W - x0);   // valid columns of this tile
     const int nrows = min(TH, g.H - y0);

@@ -77,3 +77,79 @@ def test_no_components():
     img = np.zeros((100, 130), dtype=np.uint8)
     st = gpu_stats(img, 8)
     assert st["label"].size == 0
+
+
+# ---- statistics gathered in the labelling pass (ccl_label_with_stats) ----
+
+def fused(img, conn):
+    """Labels and statistics from one ccl_label_with_stats call, the records
+    sorted by label."""
+    return ccl.label_with_stats(torch.from_numpy(np.ascontiguousarray(img)).to(DEV), conn)
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+@pytest.mark.parametrize("hw", [(1, 1), (1, 300), (300, 1), (64, 256), (65, 257), (777, 1500),
+                                (1024, 1024), (1080, 1920)])
+def test_fused_random_images(hw, conn):
+    h, w = hw
+    for k, p in enumerate((0.1, 0.3, 0.5, 0.7)):
+        img = synthetic.bernoulli(h, w, p, k, cfg_id=63)
+        labels, st = fused(img, conn)
+        want_labels = oracle.label(img, conn)
+        assert np.array_equal(labels.cpu().numpy(), want_labels), f"{h}x{w} p={p}: labels"
+        assert_stats_equal(st, oracle.component_stats(want_labels), f"fused {h}x{w} p={p}")
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_fused_structured(conn):
+    cases = list(synthetic.structured_set(1024, 1024))
+    # more border roots per tile than the shared tables hold: isolated pixels
+    # on every even column of each tile's first and last rows and on the even
+    # rows of its first column
+    h = w = 1024
+    yy, xx = np.indices((h, w))
+    many = (((yy % 64 == 0) | (yy % 64 == 63)) & (xx % 2 == 0)) | ((xx % 256 == 0) & (yy % 2 == 0))
+    cases.append(("many_border_roots", many.astype(np.uint8)))
+    for name, img in cases:
+        labels, st = fused(img, conn)
+        want_labels = oracle.label(img, conn)
+        assert np.array_equal(labels.cpu().numpy(), want_labels), name
+        assert_stats_equal(st, oracle.component_stats(want_labels), f"fused {name}")
+
+
+def test_fused_full_size_8192():
+    img = synthetic.bernoulli(8192, 8192, 0.5, 0)
+    labels, st = fused(img, 8)
+    want_labels = oracle.label(img, 8)
+    assert np.array_equal(labels.cpu().numpy(), want_labels)
+    assert_stats_equal(st, oracle.component_stats(want_labels), "fused 8192")
+
+
+def test_fused_capacity_smaller_than_count():
+    """max_comps below the count: the count is complete, max_comps records are
+    written, each exact, and nothing past them."""
+    img = synthetic.bernoulli(500, 600, 0.4, 3, cfg_id=64)
+    want = oracle.component_stats(oracle.label(img, 8))
+    n = want["label"].size
+    cap = n // 3
+    comps = torch.full((cap + 16, ccl.COMPONENT_WORDS), -77, dtype=torch.int32, device=DEV)
+    _, comps_out, ncomps = ccl.ccl_label_with_stats(torch.from_numpy(img).to(DEV), 8, cap,
+                                                    comps=comps)
+    ccl.ccl_sync()
+    assert int(ncomps.item()) == n
+    raw = comps_out.cpu().numpy()
+    assert (raw[cap:] == -77).all()
+    got = {f: raw[:cap, k].astype(np.int64) for k, f in enumerate(FIELDS[:6])}
+    wide = raw[:cap, 6:10].copy().view(np.int64)
+    got["sum_x"], got["sum_y"] = wide[:, 0], wide[:, 1]
+    idx = np.searchsorted(want["label"], got["label"])
+    assert np.array_equal(want["label"][idx], got["label"]), "a written record has no component"
+    assert np.unique(got["label"]).size == cap, "a component was written twice"
+    assert_stats_equal(got, {f: v[idx] for f, v in want.items()}, "written records")
+
+
+def test_fused_no_components():
+    img = np.zeros((100, 130), dtype=np.uint8)
+    labels, st = fused(img, 8)
+    assert st["label"].size == 0
+    assert int(labels.abs().sum().item()) == 0
