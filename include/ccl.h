@@ -305,6 +305,10 @@ ccl_status ccl_component_stats(const int32_t *d_labels, int height, int width,
  *               the call first).
  *   d_ws      : workspace of ws_bytes >= ccl_workspace_bytes_with_stats(), or
  *               NULL (library-owned).
+ * Limit beyond ccl_label's: fewer than 2^22 tiles (a tile is 256 x 64 pixels
+ * at 8-connectivity and 256 x 32 at 4 for wide images), i.e. every image of
+ * at least 512 rows, and narrower ones up to 2^30 pixels wide; larger tile
+ * counts return CCL_ERR_INVALID_ARG.
  * The local merge gives every component that stays inside a tile an output
  * record; the link phase adds each segment's count, bounding box and
  * coordinate sums (from its pixels' bits) into a per-tile table, and flushes

@@ -133,10 +133,10 @@ __global__ void __launch_bounds__(kThreads, 8) kb_link(BatchHeader *hdr, const B
         const ImageArgs a = imgs[s_img].a;
         const int tile = t - imgs[s_img].tile_off;
         switch (a.g.nw) {
-            case 1: link_tile<1, HS>(a, tile, sm, err); break;
-            case 2: link_tile<2, HS>(a, tile, sm, err); break;
-            case 4: link_tile<4, HS>(a, tile, sm, err); break;
-            default: link_tile<8, HS>(a, tile, sm, err); break;
+            case 1: link_tile<1, HS>(a, tile, sm.S, sm.c, err); break;
+            case 2: link_tile<2, HS>(a, tile, sm.S, sm.c, err); break;
+            case 4: link_tile<4, HS>(a, tile, sm.S, sm.c, err); break;
+            default: link_tile<8, HS>(a, tile, sm.S, sm.c, err); break;
         }
         __syncthreads();
     }

@@ -58,20 +58,22 @@ template <int NW, int HS>
 __global__ void __launch_bounds__(kThreads, 8) k_link(ImageArgs a, int *err) {
     __shared__ SmemLink sm;
     pdl_launch_dependents();
-    link_tile<NW, HS>(a, blockIdx.x, sm, err);
+    link_tile<NW, HS>(a, blockIdx.x, sm.S, sm.c, err);
 }
 
-// The link phase with component statistics (ccl_label_with_stats): the link
-// kernel's shared memory plus the per-tile statistics tables, dynamic.
-constexpr size_t kLinkStatsSmem = ((sizeof(SmemLink) + 15) & ~(size_t)15) + sizeof(SmemLinkStats);
+// The statistics grid of ccl_label_with_stats: the per-tile statistics tables
+// and the link phase's shared memory without its label table, dynamic.
+constexpr size_t kLinkStatsSmem = ((sizeof(SmemLinkStats) + 15) & ~(size_t)15) + sizeof(SmemLinkCore);
 
+// Statistics of every tile (ccl_label_with_stats), without the label image:
+// launched on a side stream so that it runs alongside the link kernel, which
+// is bound by HBM writes while this one reads only compact data.
 template <int NW, int HS>
-__global__ void __launch_bounds__(kThreads) k_link_stats(ImageArgs a, int *err) {
+__global__ void __launch_bounds__(kThreads, 5) k_stats_tile(ImageArgs a, int *err) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    SmemLink &sm = *reinterpret_cast<SmemLink *>(dsm);
-    SmemLinkStats *sx = reinterpret_cast<SmemLinkStats *>(dsm + ((sizeof(SmemLink) + 15) & ~(size_t)15));
-    pdl_launch_dependents();
-    link_tile<NW, HS, true>(a, blockIdx.x, sm, err, sx);
+    SmemLinkStats *sx = reinterpret_cast<SmemLinkStats *>(dsm);
+    SmemLinkCore &sm = *reinterpret_cast<SmemLinkCore *>(dsm + ((sizeof(SmemLinkStats) + 15) & ~(size_t)15));
+    link_tile<NW, HS, true, false>(a, blockIdx.x, nullptr, sm, err, sx);
 }
 
 // Statistics, last step: every border root that is its component's global
@@ -129,18 +131,14 @@ static void launch_merge_link(const ImageArgs &a, bool local_only, int *err, cud
             launch_pdl(km, (unsigned)ntiles, (unsigned)kThreads, s, a, local_only ? 1 : 0, err);
         else
             km<<<ntiles, kThreads, 0, s>>>(a, local_only ? 1 : 0, err);
-    } else if (stats) {
+    } else if (stats) {   // the statistics grid (the link itself is launched separately)
         static bool attr_set = false;   // per template instance; idempotent
         if (!attr_set) {
-            cudaFuncSetAttribute(k_link_stats<NW, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_stats_tile<NW, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kLinkStatsSmem);
             attr_set = true;
         }
-        if (link_early)
-            launch_pdl_smem(k_link_stats<NW, HS>, (unsigned)ntiles, (unsigned)kThreads,
-                            kLinkStatsSmem, s, a, err);
-        else
-            k_link_stats<NW, HS><<<ntiles, kThreads, kLinkStatsSmem, s>>>(a, err);
+        k_stats_tile<NW, HS><<<ntiles, kThreads, kLinkStatsSmem, s>>>(a, err);
     } else if (link_early) {
         launch_pdl(k_link<NW, HS>, (unsigned)ntiles, (unsigned)kThreads, s, a, err);
     } else {
@@ -229,6 +227,8 @@ ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, in
     size_t need = default_tile ? ccl_workspace_bytes(height, width, conn)
                                : bits_bytes(g) + tiles_bytes(g);
     if (so) {
+        // the statistics name a global root by (tile, slot) in 32 bits
+        if ((long long)g.tiles_x * g.tiles_y >= (1ll << (32 - kSlotBits))) return CCL_ERR_INVALID_ARG;
         if (!so->comps && so->max_comps > 0) return CCL_ERR_INVALID_ARG;
         if (!so->ncomps || so->max_comps < 0 || (flags & CCL_FLAG_LOCAL_ONLY) || level >= 0)
             return CCL_ERR_INVALID_ARG;
@@ -288,8 +288,23 @@ ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, in
             k_seams<<<(unsigned)blocks, 256, 0, stream>>>(a, items, err);
     }
     if (timed) cudaEventRecord(t_phase_events[2], stream);
-    launch_tile_kernel(a, local_only, err, stream, true, seams, so != nullptr);
-    if (so) k_stats_pack<<<(unsigned)(g.tiles_x * g.tiles_y), 256, 0, stream>>>(a, err);
+    if (so) {
+        // statistics on a side stream, alongside the link kernel; joined before
+        // the pack kernel (the event between the seam and link kernels means
+        // the link kernel does not start early here)
+        SideStream side;
+        if (!side_stream(stream, &side)) return CCL_ERR_CUDA;
+        if (cudaEventRecord(side.fork, stream) != cudaSuccess ||
+            cudaStreamWaitEvent(side.stream, side.fork, 0) != cudaSuccess)
+            return CCL_ERR_CUDA;
+        launch_tile_kernel(a, false, err, side.stream, true, false, true);
+        if (cudaEventRecord(side.join, side.stream) != cudaSuccess) return CCL_ERR_CUDA;
+        launch_tile_kernel(a, local_only, err, stream, true, false, false);
+        if (cudaStreamWaitEvent(stream, side.join, 0) != cudaSuccess) return CCL_ERR_CUDA;
+        k_stats_pack<<<(unsigned)(g.tiles_x * g.tiles_y), 256, 0, stream>>>(a, err);
+    } else {
+        launch_tile_kernel(a, local_only, err, stream, true, seams, false);
+    }
     if (timed) cudaEventRecord(t_phase_events[3], stream);
     if (cudaGetLastError() != cudaSuccess) return CCL_ERR_CUDA;
     return CCL_OK;

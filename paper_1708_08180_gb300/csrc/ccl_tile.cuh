@@ -7,6 +7,11 @@
 
 namespace ccl {
 
+// Statistics (ccl_label_with_stats): components aggregated per tile in shared
+// memory; the ones past these tables are added straight into global memory.
+constexpr int kStatLocal = 128;    // components inside the tile
+constexpr int kStatBorder = 128;   // global roots of the tile's border roots
+
 // One image as the kernels see it.
 struct ImageArgs {
     const uint8_t *img;
@@ -71,27 +76,37 @@ struct SmemMerge {
     int out_base;                  // statistics: their first output record
 };
 
-// Shared memory of the link phase.
-struct SmemLink {
-    __align__(16) int S[kNodeCap];   // label per segment node
+// Shared memory of the link phase: the label of every segment node (the
+// statistics-only grid has none) and the rest.
+struct SmemLinkCore {
     int R[kBorderCapMax];         // final label per border root
     uint32_t rows[2 * kThreads];  // bit rows of the tile: [row][word]
     uint32_t st[kThreads];        // segment starts per (strip, word)
     int base[kThreads];           // rank of the word's first segment start
     int warp_sums[kThreads / 32];
 };
+struct SmemLink {
+    __align__(16) int S[kNodeCap];   // label per segment node
+    SmemLinkCore c;
+};
 
 // Statistics mode of the link phase: per-tile aggregates of the components
 // the tile's segments belong to (tile coordinates), flushed once per tile.
-constexpr int kStatLocal = 128;    // components inside the tile aggregated in shared memory
-constexpr int kStatBorder = 128;   // global roots (of border roots) aggregated in shared memory
 constexpr int kStatHash = 1024;    // global roots of a tile's border roots (hash table)
+// A global forest node without its key: tile << kSlotBits | slot (tiles of
+// at least 8192 pixels: fewer than 2^18 per image, so this fits 32 bits).
+__device__ __forceinline__ uint32_t gnode_site(gnode r) {
+    return (uint32_t)(r & ((1ull << (kTileBits + kSlotBits)) - 1ull));
+}
+constexpr uint32_t kNoSite = 0xFFFFFFFFu;
+
 struct SmemLinkStats {
     __align__(16) uint16_t C[kNodeCap];       // component slot per segment node (cslot encoding)
-    gnode G[kBorderCapMax];                   // global root of each border root
-    gnode HK[kStatHash];                      // hash table: the distinct global roots ...
+    uint32_t G[kBorderCapMax];                // global root (site) of each border root
+    uint32_t HK[kStatHash];                   // hash table: the distinct global roots ...
     uint16_t HV[kStatHash];                   // ... and their aggregate index in the tile
     uint16_t HJ[kBorderCapMax];               // each border root's hash entry
+    uint16_t HR[kBorderCapMax];               // each aggregate index's hash entry
     unsigned LA[kStatLocal][7];               // count, xmin, ymin, xmax, ymax, sum x, sum y
     unsigned BA[kStatBorder][7];              // per global root
     int nroots;                               // distinct global roots in the tile
@@ -463,13 +478,17 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             if (r == n && !f) {
                 const long long o = (long long)ob + lslot[n];
                 if (o < a.max_comps) {
-                    CompRec c;
-                    c.label = 1 + gkey(k);
-                    c.count = 0;
-                    c.xmin = c.ymin = 0x7FFFFFFF;
-                    c.xmax = c.ymax = -1;
-                    c.sum_x = c.sum_y = 0;
-                    recs[o] = c;
+                    if (lslot[n] < kStatLocal) {   // the statistics flush writes the rest
+                        recs[o].label = 1 + gkey(k);
+                    } else {                       // added into with atomics: initialise
+                        CompRec c;
+                        c.label = 1 + gkey(k);
+                        c.count = 0;
+                        c.xmin = c.ymin = 0x7FFFFFFF;
+                        c.xmax = c.ymax = -1;
+                        c.sum_x = c.sum_y = 0;
+                        recs[o] = c;
+                    }
                 }
             }
         }
@@ -769,9 +788,12 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
 // give every segment its final label (its local root's, or the resolved label
 // of its border root), and write one int32 per pixel.  The stores are laid
 // out so that 32 lanes write 128 consecutive pixels (512 bytes) of one row.
-template <int NW, int HS, bool STATS = false>
-__device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink &sm, int *err,
-                                          SmemLinkStats *sx = nullptr) {
+// STATS: gather the component statistics of the tile (ccl_label_with_stats);
+// LABELS: write the label image.  The statistics run as a separate grid with
+// LABELS false, concurrently with the plain link (LABELS true, STATS false).
+template <int NW, int HS, bool STATS = false, bool LABELS = true>
+__device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, int *S, SmemLinkCore &sm,
+                                          int *err, SmemLinkStats *sx = nullptr) {
     constexpr int NS = kThreads / NW;
     constexpr int TW = 32 * NW;
     constexpr int TH = NS * HS;
@@ -794,8 +816,8 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
     // the per-segment labels, copied to shared memory asynchronously
     // (16-byte cp.async; the source starts 16 bytes into the 256-byte aligned
     // tile workspace, and rounding the count up stays inside the workspace)
-    for (int c = tid; c < (nseg + 3) / 4; c += kThreads) {
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(&sm.S[4 * c]);
+    for (int c = tid; LABELS && c < (nseg + 3) / 4; c += kThreads) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(&S[4 * c]);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
                      "l"(tw_ + kHdrInts + 4 * c) : "memory");
     }
@@ -814,7 +836,7 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
             e[3] = e[4] = 0u;
             e[5] = e[6] = 0u;
         }
-        for (int i = tid; i < kStatHash; i += kThreads) sx->HK[i] = kNoNode;
+        for (int i = tid; i < kStatHash; i += kThreads) sx->HK[i] = kNoSite;
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 #pragma unroll
@@ -841,7 +863,7 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
                 r = p;
             }
             sm.R[j] = 1 + gnode_key(r);
-            if (STATS) sx->G[j] = r;
+            if (STATS) sx->G[j] = gnode_site(r);
         }
     }
     int total;
@@ -853,11 +875,16 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
         // aggregate: a hash table on the global root gives each distinct root
         // an index, taken by the thread that inserts it
         for (int j = tid; j < nb; j += kThreads) {
-            const gnode r = sx->G[j];
-            unsigned h = (unsigned)((r ^ (r >> 29)) * 0x9E3779B1u) & (kStatHash - 1);
+            const uint32_t r = sx->G[j];
+            unsigned h = (r * 0x9E3779B1u) >> 22;   // 10 bits: kStatHash entries
             for (int probe = 0; probe < kStatHash; ++probe, h = (h + 1) & (kStatHash - 1)) {
-                const gnode old = atomicCAS(&sx->HK[h], kNoNode, r);
-                if (old == kNoNode) { sx->HV[h] = (uint16_t)atomicAdd(&sx->nroots, 1); break; }
+                const uint32_t old = atomicCAS(&sx->HK[h], kNoSite, r);
+                if (old == kNoSite) {
+                    const int id = atomicAdd(&sx->nroots, 1);
+                    sx->HV[h] = (uint16_t)id;
+                    sx->HR[id] = (uint16_t)h;
+                    break;
+                }
                 if (old == r) break;
             }
             sx->HJ[j] = (uint16_t)h;
@@ -866,14 +893,14 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();   // every thread's copies of S have landed
     if (total != nseg) { if (tid == 0) atomicOr(err, kErrBorderCap); }
-    for (int n = tid; n < total; n += kThreads) {
-        const int v = sm.S[n];
+    for (int n = tid; LABELS && n < total; n += kThreads) {
+        const int v = S[n];
         if (v < 0) {
             const int j = -v - 1;
             if (j < nb) {
-                sm.S[n] = sm.R[j];
+                S[n] = sm.R[j];
             } else {
-                sm.S[n] = 0;
+                S[n] = 0;
                 atomicOr(err, kErrBorderCap);
             }
         }
@@ -891,105 +918,133 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
         const int ob = __ldcg(tw_ + 2), nloc = __ldcg(tw_ + 3);
         CompRec *recs = static_cast<CompRec *>(a.comps);
         BorderAcc *bacc = static_cast<BorderAcc *>(a.bacc);
-        auto root_acc = [&](gnode r) {
-            const long long rt = (long long)((r >> kSlotBits) & (kMaxTiles - 1));
-            return bacc + (size_t)rt * g.border_cap + (int)(r & ((1u << kSlotBits) - 1u));
+        auto root_acc = [&](uint32_t r) {   // a global root's site
+            return bacc + (size_t)(r >> kSlotBits) * g.border_cap + (int)(r & ((1u << kSlotBits) - 1u));
         };
-        // Pieces are taken one per lane per step (warp-uniform trip count);
-        // lanes whose pieces belong to the same component (a border root is
-        // replaced by its tile representative) combine their values with warp
-        // reductions, and one lane per component updates the aggregate.
-        const int rep_hi = kStatBorder;
+        // A thread adds up its pieces in registers: one accumulator for the
+        // first component it meets that crosses the tile border (in a dense
+        // image, the large component most pieces belong to) and one for the
+        // current run of pieces of any other component, flushed when the
+        // component changes.  The crossing one is flushed at the end with warp
+        // reductions among the lanes that hold the same component.
+        struct Agg {
+            int c;   // component: >= 0 inside the tile, < 0: -(1 + aggregate index)
+            unsigned cnt, xmn, ymn, xmx, ymx, sx, sy;
+        };
+        auto add_to = [&](Agg &d, unsigned cnt, unsigned xmn, unsigned ymn, unsigned xmx,
+                          unsigned ymx, unsigned sxl, unsigned syl) {
+            d.cnt += cnt;
+            d.xmn = min(d.xmn, xmn);
+            d.ymn = min(d.ymn, ymn);
+            d.xmx = max(d.xmx, xmx);
+            d.ymx = max(d.ymx, ymx);
+            d.sx += sxl;
+            d.sy += syl;
+        };
+        // one aggregate into the shared tables, or its global record when
+        // the tables are full
+        auto flush = [&](const Agg &d) {
+            const int c = d.c;
+            unsigned *e = nullptr;
+            if (c >= 0 && c < kStatLocal) e = sx->LA[c];
+            else if (c < 0 && -c - 1 < kStatBorder) e = sx->BA[-c - 1];
+            if (e) {
+                atomicAdd(e + 0, d.cnt);
+                atomicMin(e + 1, d.xmn);
+                atomicMin(e + 2, d.ymn);
+                atomicMax(e + 3, d.xmx);
+                atomicMax(e + 4, d.ymx);
+                atomicAdd(e + 5, d.sx);
+                atomicAdd(e + 6, d.sy);
+            } else if (c >= 0) {   // a component inside the tile, past the shared table
+                if ((long long)ob + c < a.max_comps) {
+                    CompRec *rc = recs + ob + c;
+                    atomicAdd(&rc->count, (int)d.cnt);
+                    atomicMin(&rc->xmin, x0 + (int)d.xmn);
+                    atomicMin(&rc->ymin, y0 + (int)d.ymn);
+                    atomicMax(&rc->xmax, x0 + (int)d.xmx);
+                    atomicMax(&rc->ymax, y0 + (int)d.ymx);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&rc->sum_x),
+                              (unsigned long long)d.sx + (unsigned long long)x0 * d.cnt);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&rc->sum_y),
+                              (unsigned long long)d.sy + (unsigned long long)y0 * d.cnt);
+                }
+            } else {               // a global root past the shared table
+                const int id = -c - 1;
+                if (id < nb) {
+                    BorderAcc *tacc = root_acc(sx->HK[sx->HR[id]]);
+                    atomicAdd(&tacc->count, d.cnt);
+                    atomicMin(&tacc->xmin, x0 + (int)d.xmn);
+                    atomicMin(&tacc->ymin, y0 + (int)d.ymn);
+                    atomicMax(&tacc->xmax, x0 + (int)d.xmx);
+                    atomicMax(&tacc->ymax, y0 + (int)d.ymx);
+                    atomicAdd(&tacc->sum_x, (unsigned long long)d.sx + (unsigned long long)x0 * d.cnt);
+                    atomicAdd(&tacc->sum_y, (unsigned long long)d.sy + (unsigned long long)y0 * d.cnt);
+                }
+            }
+        };
+        Agg A{0x7FFFFFFF, 0u, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u, 0u};
+        Agg B = A;
         const bool has_pre = mL && (m & 1u) && base >= 1;
         const uint32_t pre = has_pre ? (m & ~(m + 1u)) : 0u;   // run continuing from the word before
-        const int npieces = __popc(st) + (has_pre ? 1 : 0);
-        const int trips = __reduce_max_sync(0xFFFFFFFFu, npieces);
         uint32_t rem = st;
         bool pre_left = has_pre;
         int n_next = base;
-        const int lane = tid & 31;
-        for (int t = 0; t < trips; ++t) {
-            int n = -1;
-            uint32_t mask = 0u;
+        while (pre_left || rem) {
+            int n;
+            uint32_t mask;
             if (pre_left) {
                 n = base - 1;
                 mask = pre;
                 pre_left = false;
-            } else if (rem) {
+            } else {
                 const int i = __ffs(rem) - 1;
                 rem &= rem - 1;
                 const uint32_t z = ~m & (0xFFFFFFFFu << i);
                 const int end = z ? __ffs(z) - 1 : 32;
                 mask = __funnelshift_lc(0xFFFFFFFFu, 0u, (unsigned)end) & (0xFFFFFFFFu << i);
                 n = n_next++;
-                if (n >= total) n = -1;
+                if (n >= total) continue;
             }
-            const bool act = n >= 0;
-            const unsigned am = __ballot_sync(0xFFFFFFFFu, act);
-            if (!act) continue;
             const uint32_t tt = rows[0] & mask, bb = HS == 2 ? (rows[HS - 1] & mask) : 0u;
             const uint32_t any = tt | bb;
             const int ct = __popc(tt), cb = __popc(bb), cnt = ct + cb;
             const int xw = 32 * w, ys = s * HS;
-            unsigned sxl = (unsigned)(xw * cnt + bit_position_sum(tt) + bit_position_sum(bb));
-            unsigned syl = (unsigned)(ys * ct + (ys + 1) * cb);
-            unsigned xmn = (unsigned)(xw + __ffs(any) - 1), xmx = (unsigned)(xw + 31 - __clz(any));
-            unsigned ymn = ct ? ys : ys + 1, ymx = cb ? ys + 1 : ys;
-            unsigned ucnt = (unsigned)cnt;
-            // c >= 0: a component inside the tile; c < 0: -(1 + aggregate index)
-            // of a global root (the hash entry of its border root)
+            const unsigned sxl = (unsigned)(xw * cnt + bit_position_sum(tt) + bit_position_sum(bb));
+            const unsigned syl = (unsigned)(ys * ct + (ys + 1) * cb);
+            const unsigned xmn = (unsigned)(xw + __ffs(any) - 1), xmx = (unsigned)(xw + 31 - __clz(any));
+            const unsigned ymn = ct ? ys : ys + 1, ymx = cb ? ys + 1 : ys;
             const unsigned cv = sx->C[n];
             int c = (int)cv;
-            unsigned hslot = 0u;
             if (cv & kSlotBorder) {
                 const int j = (int)(cv & (kSlotBorder - 1u));
-                hslot = sx->HJ[j < nb ? j : 0];
-                c = -1 - (int)sx->HV[hslot];
+                c = -1 - (int)sx->HV[sx->HJ[j < nb ? j : 0]];
             }
-            const unsigned gm = __match_any_sync(am, c);
-            ucnt = __reduce_add_sync(gm, ucnt);
-            sxl = __reduce_add_sync(gm, sxl);
-            syl = __reduce_add_sync(gm, syl);
-            xmn = __reduce_min_sync(gm, xmn);
-            ymn = __reduce_min_sync(gm, ymn);
-            xmx = __reduce_max_sync(gm, xmx);
-            ymx = __reduce_max_sync(gm, ymx);
-            if (lane != __ffs(gm) - 1) continue;
-            unsigned *e = nullptr;
-            if (c >= 0 && c < kStatLocal) e = sx->LA[c];
-            else if (c < 0 && -c - 1 < rep_hi) e = sx->BA[-c - 1];
-            if (e) {
-                atomicAdd(e + 0, ucnt);
-                atomicMin(e + 1, xmn);
-                atomicMin(e + 2, ymn);
-                atomicMax(e + 3, xmx);
-                atomicMax(e + 4, ymx);
-                atomicAdd(e + 5, sxl);
-                atomicAdd(e + 6, syl);
-            } else if (c >= 0) {   // a component inside the tile, past the shared table
-                if ((long long)ob + c < a.max_comps) {
-                    CompRec *rc = recs + ob + c;
-                    atomicAdd(&rc->count, (int)ucnt);
-                    atomicMin(&rc->xmin, x0 + (int)xmn);
-                    atomicMin(&rc->ymin, y0 + (int)ymn);
-                    atomicMax(&rc->xmax, x0 + (int)xmx);
-                    atomicMax(&rc->ymax, y0 + (int)ymx);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&rc->sum_x),
-                              (unsigned long long)sxl + (unsigned long long)x0 * ucnt);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&rc->sum_y),
-                              (unsigned long long)syl + (unsigned long long)y0 * ucnt);
+            if (c < 0 && B.c == 0x7FFFFFFF) B.c = c;
+            if (c == B.c) {
+                add_to(B, (unsigned)cnt, xmn, ymn, xmx, ymx, sxl, syl);
+            } else {
+                if (c != A.c) {
+                    if (A.c != 0x7FFFFFFF) flush(A);
+                    A = Agg{c, 0u, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u, 0u};
                 }
-            } else {               // a global root past the shared table
-                {
-                    BorderAcc *tacc = root_acc(sx->HK[hslot]);
-                    atomicAdd(&tacc->count, ucnt);
-                    atomicMin(&tacc->xmin, x0 + (int)xmn);
-                    atomicMin(&tacc->ymin, y0 + (int)ymn);
-                    atomicMax(&tacc->xmax, x0 + (int)xmx);
-                    atomicMax(&tacc->ymax, y0 + (int)ymx);
-                    atomicAdd(&tacc->sum_x, (unsigned long long)sxl + (unsigned long long)x0 * ucnt);
-                    atomicAdd(&tacc->sum_y, (unsigned long long)syl + (unsigned long long)y0 * ucnt);
-                }
+                add_to(A, (unsigned)cnt, xmn, ymn, xmx, ymx, sxl, syl);
+            }
+        }
+        if (A.c != 0x7FFFFFFF) flush(A);
+        {
+            const bool hb = B.c != 0x7FFFFFFF;
+            const unsigned am = __ballot_sync(0xFFFFFFFFu, hb);
+            if (hb) {
+                const unsigned gm = __match_any_sync(am, B.c);
+                B.cnt = __reduce_add_sync(gm, B.cnt);
+                B.sx = __reduce_add_sync(gm, B.sx);
+                B.sy = __reduce_add_sync(gm, B.sy);
+                B.xmn = __reduce_min_sync(gm, B.xmn);
+                B.ymn = __reduce_min_sync(gm, B.ymn);
+                B.xmx = __reduce_max_sync(gm, B.xmx);
+                B.ymx = __reduce_max_sync(gm, B.ymx);
+                if ((tid & 31) == __ffs(gm) - 1) flush(B);
             }
         }
         __syncthreads();
@@ -1007,8 +1062,8 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
             rc->sum_y = (long long)e[6] + (long long)y0 * cnt;
         }
         for (int h = tid; h < kStatHash; h += kThreads) {
-            const gnode r = sx->HK[h];
-            if (r == kNoNode || sx->HV[h] >= kStatBorder) continue;
+            const uint32_t r = sx->HK[h];
+            if (r == kNoSite || sx->HV[h] >= kStatBorder) continue;
             const unsigned *e = sx->BA[sx->HV[h]];
             if (e[0] == 0u) continue;
             BorderAcc *t = root_acc(r);
@@ -1022,6 +1077,7 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
         }
     }
 
+    if (!LABELS) return;
     const int ncols = min(TW, g.W - x0);   // valid columns of this tile
     const int nrows = min(TH, g.H - y0);
     if (a.out_aligned16 && (ncols & 3) == 0) {
@@ -1045,7 +1101,7 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (e > 0) cur += (sq >> (b0 + e)) & 1u;
-                if ((rb >> (b0 + e)) & 1u) v[e] = sm.S[cur < 0 ? 0 : cur];
+                if ((rb >> (b0 + e)) & 1u) v[e] = S[cur < 0 ? 0 : cur];
             }
             __stcs(reinterpret_cast<int4 *>(out), make_int4(v[0], v[1], v[2], v[3]));
         }
@@ -1076,7 +1132,7 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, SmemLink
                     const int o = (r / HS) * NW + wq;
                     if ((sm.rows[r * NW + wq] >> b) & 1u) {
                         const int cur = sm.base[o] + __popc(sm.st[o] & le_mask(b)) - 1;
-                        v[e] = sm.S[cur < 0 ? 0 : cur];
+                        v[e] = S[cur < 0 ? 0 : cur];
                     } else if (a.merge_out) {
                         v[e] = row[c];   // keep the pixels this pass does not label
                     }
