@@ -898,6 +898,8 @@ def main(argv=None) -> int:
     ap.add_argument("--no-volume", action="store_true", help="skip the 3-D volume leg")
     ap.add_argument("--served-full", action="store_true",
                     help="run only the serving sweep (1k-20k req/s, 10 s or 20k requests each)")
+    ap.add_argument("--stats-only", action="store_true",
+                    help="run only the component-statistics legs (one JSON line)")
     ap.add_argument("--cpu-sweep", action="store_true",
                     help="run only the CPU oracle over the density sweep and structured set")
     ap.add_argument("--volume-only", action="store_true",
@@ -937,6 +939,8 @@ def main(argv=None) -> int:
         return run_volume_only(args, local)
     if args.served_full:
         return run_served_full(args, local)
+    if args.stats_only:
+        return run_stats_only(args, local)
     if args.cpu_sweep:
         return run_cpu_sweep(args)
     return run_ours(args, rank, world, local)
@@ -999,6 +1003,37 @@ def run_cpu_sweep(args) -> int:
         for conn in (4, 8):
             out["structured_4096"][f"{name}_conn{conn}"] = round(med3(img, conn), 2)
     print(json.dumps({"cpu_sweep": out}), flush=True)
+    return 0
+
+
+def run_stats_only(args, local) -> int:
+    """Only the statistics legs on the headline images (ccl_component_stats
+    after labelling, and ccl_label_with_stats), one JSON line."""
+    import torch
+
+    import paper_1708_08180_gb300 as ccl
+    import synthetic
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ccl.load()
+    stream = torch.cuda.current_stream(dev)
+    imgs = [torch.from_numpy(synthetic.bernoulli(H, W, P, seed=r)).to(dev) for r in range(ROTATE)]
+    outs = [torch.empty((H, W), dtype=torch.int32, device=dev) for _ in range(ROTATE)]
+    ws = torch.empty(ccl.ccl_workspace_bytes(H, W, CONN), dtype=torch.uint8, device=dev)
+    for k in range(3):
+        ccl.ccl_label(imgs[k % ROTATE], CONN, out=outs[k % ROTATE], ws=ws, stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(20):
+        ccl.ccl_label(imgs[k % ROTATE], CONN, out=outs[k % ROTATE], ws=ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    label_ms = e0.elapsed_time(e1) / 20
+    res = {"label_ms": round(label_ms, 5), "component_stats": stats_leg(outs[0], stream),
+           "label_with_stats": fused_stats_leg(imgs, outs, label_ms, stream)}
+    print(json.dumps(res), flush=True)
     return 0
 
 

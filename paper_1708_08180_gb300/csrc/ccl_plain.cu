@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kThreads) k_merge(ImageArgs a, int local_only,
     merge_tile<NW, HS, STATS>(a, blockIdx.x, local_only != 0, sm, err);
 }
 
-__global__ void __launch_bounds__(256, 4) k_seams(ImageArgs a, long long nitems, int *err) {
+__global__ void __launch_bounds__(256, 5) k_seams(ImageArgs a, long long nitems, int *err) {
     __shared__ SmemSeams sm;
     pdl_wait();
     pdl_launch_dependents();

@@ -1107,44 +1107,18 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, int *S, 
         }
     } else {
         // rows not 16-byte aligned (W % 4 != 0 or an unaligned label pointer):
-        // chunks of 4 labels at 16-byte aligned addresses, so that the inside
-        // of every row is written with 16-byte stores and only the chunks
-        // that overhang the row's ends with single ones.  The head of a row
-        // is the number of labels between its start and the 16-byte boundary
-        // below it; a chunk's 4 pixels may then straddle two bit words.
-        constexpr int CPR = TW / 4 + 1;
-        for (int id = tid; id < TH * CPR; id += kThreads) {
-            const int r = id / CPR, k = id % CPR;
-            if (r >= nrows) continue;
-            int32_t *row = a.labels + (size_t)(y0 + r) * g.W + x0;
-            const int head = (int)((reinterpret_cast<uintptr_t>(row) >> 2) & 3u);
-            const int c0 = 4 * k - head;   // tile column of the chunk's first label
-            if (c0 >= ncols) continue;
-            int v[4];
-            bool in[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int c = c0 + e;
-                in[e] = c >= 0 && c < ncols;
-                v[e] = 0;
-                if (in[e]) {
-                    const int wq = c >> 5, b = c & 31;
-                    const int o = (r / HS) * NW + wq;
-                    if ((sm.rows[r * NW + wq] >> b) & 1u) {
-                        const int cur = sm.base[o] + __popc(sm.st[o] & le_mask(b)) - 1;
-                        v[e] = S[cur < 0 ? 0 : cur];
-                    } else if (a.merge_out) {
-                        v[e] = row[c];   // keep the pixels this pass does not label
-                    }
-                }
-            }
-            if (in[0] && in[3]) {
-                __stcs(reinterpret_cast<int4 *>(row + c0), make_int4(v[0], v[1], v[2], v[3]));
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (in[e]) row[c0 + e] = v[e];
-            }
+        // one label per thread and step, 32 lanes writing 128 consecutive bytes
+        for (int id = tid; id < TH * TW; id += kThreads) {
+            const int r = id / TW, c = id % TW;
+            if (r >= nrows || c >= ncols) continue;
+            const int wq = c >> 5, b = c & 31;
+            const int o = (r / HS) * NW + wq;
+            const uint32_t rb = sm.rows[r * NW + wq];
+            const uint32_t sq = sm.st[o];
+            const int cur = sm.base[o] + __popc(sq & le_mask(b)) - 1;
+            int32_t *out = a.labels + (size_t)(y0 + r) * g.W + x0 + c;
+            if ((rb >> b) & 1u) *out = S[cur < 0 ? 0 : cur];
+            else if (!a.merge_out) *out = 0;
         }
     }
 }
