@@ -198,7 +198,11 @@ void ccl_set_phase_events(void *const *events);
  * asynchronous CUDA error. */
 ccl_status ccl_sync(ccl_stream stream);
 
-/* Free library-owned workspaces and batched-path state on every device. */
+/* Free library-owned workspaces, side streams and batched-path state on every
+ * device, and forget the device addresses the library caches per device (its
+ * error word, the scratch array of ccl_label_static).  Call it after a
+ * device's context was reset (cudaDeviceReset) and before using the library
+ * on that device again: the cached addresses belong to the old context. */
 ccl_status ccl_shutdown(void);
 
 /* ---- failure injection (for tests of the failure paths) ------------------
@@ -241,7 +245,9 @@ ccl_status ccl_inject_alloc_failures(int count);
  *     nothing is enqueued.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current) and caches it; make
- *     that first call before any stream capture.
+ *     that first call before any stream capture.  Later calls read the cache
+ *     without locking.  ccl_shutdown() forgets it (needed after a context
+ *     reset, which moves the array).
  *   - All calls on a device share the one array and it keeps the previous
  *     call's contents (nothing in it needs clearing: every word is written
  *     before it is read).  Calls whose work overlaps on the GPU (different

@@ -15,6 +15,9 @@ namespace ccl {
 // Device address of the current device's error word (set up once per device).
 int *device_error_word();
 
+// Forget the cached device addresses of the allocation-free scratch array.
+void forget_static_scratch();
+
 // Library-owned workspace for (current device, stream), grown to >= bytes.
 void *library_workspace(cudaStream_t stream, size_t bytes, ccl_status *st);
 

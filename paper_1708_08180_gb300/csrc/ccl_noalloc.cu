@@ -7,7 +7,7 @@
 // is only a stand-in symbol); its device address is fetched once per device
 // with cudaGetSymbolAddress, with that device current, on the first call made
 // on that device, and cached.
-#include <mutex>
+#include <atomic>
 
 #include "ccl_internal.h"
 
@@ -17,23 +17,27 @@ static __device__ __align__(256) unsigned char g_static_scratch[CCL_STATIC_SCRAT
 
 namespace {
 constexpr int kMaxDevices = 64;
-std::mutex g_static_mu;
-void *g_static_ptr[kMaxDevices] = {};
+std::atomic<void *> g_static_ptr[kMaxDevices];   // zero-initialised (static storage)
 }  // namespace
 
 // Device address of this device's copy of the scratch array (nullptr on error).
+// Lock-free after the first call on a device; two first calls racing both look
+// the address up and store the same value.
 static void *static_scratch_address(int dev) {
     if (dev < 0 || dev >= kMaxDevices) return nullptr;
-    std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        g_static_ptr[dev] = p;
+    void *p = g_static_ptr[dev].load(std::memory_order_acquire);
+    if (p) return p;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
     }
-    return g_static_ptr[dev];
+    g_static_ptr[dev].store(p, std::memory_order_release);
+    return p;
+}
+
+// Forget the cached addresses (a reset device gets new ones).
+void forget_static_scratch() {
+    for (auto &p : g_static_ptr) p.store(nullptr, std::memory_order_release);
 }
 
 }  // namespace ccl

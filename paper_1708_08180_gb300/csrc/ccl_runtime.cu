@@ -19,21 +19,22 @@ std::atomic<int> g_hops_smem{kSmemHopBudget};
 std::atomic<int> g_hops_glob{kGlobHopBudget};
 std::atomic<int> g_fail_allocs{0};
 std::mutex g_mu;
-std::map<int, int *> g_err_ptr;                                   // device -> address
+constexpr int kMaxDevices = 64;
+std::atomic<int *> g_err_ptr[kMaxDevices];                        // device -> address
 std::map<std::pair<int, cudaStream_t>, std::pair<void *, size_t>> g_ws;  // library workspaces
 std::map<std::pair<int, cudaStream_t>, SideStream> g_side;                 // side streams
 }  // namespace
 
 int *device_error_word() {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_err_ptr.find(dev);
-    if (it != g_err_ptr.end()) return it->second;
-    int *p = nullptr;
-    if (cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_ccl_error_word) != cudaSuccess)
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    int *p = g_err_ptr[dev].load(std::memory_order_acquire);
+    if (p) return p;
+    if (cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_ccl_error_word) != cudaSuccess) {
+        cudaGetLastError();
         return nullptr;
-    g_err_ptr[dev] = p;
+    }
+    g_err_ptr[dev].store(p, std::memory_order_release);
     return p;
 }
 
@@ -172,6 +173,8 @@ extern "C" ccl_status ccl_inject_alloc_failures(int count) {
 extern "C" ccl_status ccl_shutdown(void) {
     ccl::free_library_workspaces();
     ccl::free_batched_state();
+    ccl::forget_static_scratch();
+    for (auto &p : ccl::g_err_ptr) p.store(nullptr, std::memory_order_release);
     return CCL_OK;
 }
 
