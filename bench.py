@@ -263,6 +263,39 @@ def run_reference(args, rank, world):
     return 0
 
 
+def host_link_gbs(device_index: int, reps: int = 5):
+    """The host link's bandwidth: one 256 MiB device-to-host and one 64 MiB
+    host-to-device copy of pinned memory (CUDA events, best of `reps`), and
+    both directions at once."""
+    import torch
+
+    dev = torch.device("cuda", device_index)
+    d_big = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    d_small = torch.empty(64 << 20, dtype=torch.uint8, device=dev)
+    h_big = torch.empty(256 << 20, dtype=torch.uint8).pin_memory()
+    h_small = torch.empty(64 << 20, dtype=torch.uint8).pin_memory()
+    s = torch.cuda.Stream(dev)
+
+    def best(fn):
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            with torch.cuda.stream(s):
+                fn()
+            e1.record(s)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts)
+
+    d2h = best(lambda: h_big.copy_(d_big, non_blocking=True))
+    h2d = best(lambda: d_small.copy_(h_small, non_blocking=True))
+    both = best(lambda: (h_big.copy_(d_big, non_blocking=True), d_small.copy_(h_small, non_blocking=True)))
+    return {"d2h_gb_s": round((256 << 20) / d2h / 1e6, 1), "h2d_gb_s": round((64 << 20) / h2d / 1e6, 1),
+            "both_gb_s": round((320 << 20) / both / 1e6, 1)}
+
+
 def e2e_server(img_np, steps: int, device_index: int):
     """Same metric through the server's C ABI with pinned host buffers: every
     request copies its image host-to-device and its labels device-to-host."""
@@ -856,6 +889,12 @@ def run_ours(args, rank, world, local):
     }
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e_server(host_imgs[0], K, local)
+        link = host_link_gbs(local)
+        ceiling = link["both_gb_s"] / PATH_BYTES_PER_PX   # Gpx/s the link allows at 5 B/px
+        line["e2e"]["host_link"] = dict(link, gpix_s_ceiling=round(ceiling, 2),
+                                        frac=round(line["e2e"]["value"] / ceiling, 3),
+                                        what="pinned copies, CUDA events; the ceiling moves "
+                                             "1 B/px in and 4 B/px out over the measured link")
     if rank == 0 and not args.no_small:
         line["small_512"] = small_leg(dev, stream)
     if rank == 0 and not args.no_structured:
