@@ -9,7 +9,9 @@
 //     16 x 16 strips; thread t of a block owns strip (t % 16, t / 16).
 //   * local merge (Kernel 1, §II-A): a block joins the segments of its brick in
 //     shared memory, each strip with its earlier neighbour strips through the
-//     rows that face each other;
+//     rows that face each other: one contact per segment of either strip,
+//     first contacts as parent links, the other contacts queued and unioned
+//     by the whole block;
 //   * boundary analysis (Kernel 2, §II-B): threads over the rows and strips that
 //     meet a brick face union the segments that touch across it, in a global
 //     forest over the bricks' border roots (one kernel for the x faces, one for
@@ -203,6 +205,50 @@ __device__ __forceinline__ void touching_bits(uint32_t a, uint32_t b, int dil, F
     }
 }
 
+// Rank of the segment holding bit u of a strip whose segment starts are st and
+// whose first segment has rank base.
+__device__ __forceinline__ int seg_rank3(int base, uint32_t st, int u) {
+    return base + __popc(st & le_mask(u)) - 1;
+}
+
+// Lowest set bit of v among bits u - 1, u and u + 1 (one of them is set).
+__device__ __forceinline__ int low3(uint32_t v, int u) {
+    return u - 2 + __ffs(__funnelshift_r(v << 1, v >> 31, u) & 7u);
+}
+
+// Contacts of two neighbouring strips A and B at the level of their segments
+// (the runs of each strip's OR).  Facing rows fa, fb, x reach dil.  For every
+// segment of A that touches B, its pick is the segment of B holding the lowest
+// B voxel it touches; that voxel lies within one of the segment's lowest
+// touching voxel, which the carry of (segA & ~X) + stA marks (X = the voxels
+// of fa that touch fb).  Likewise for every segment of B.  Segments of a strip
+// are separated by empty voxels and touch only within dil <= 1, so two touching
+// pairs never cross (A left of A' and B right of B'); hence if neither A nor B
+// picks the other, their picks would form a crossing pair, and the picks are
+// exactly the touching pairs, with repeats.  Pairs in increasing position
+// order are non-decreasing in both segments, so every repeat follows its
+// first occurrence directly.  f(u, v) gets voxel u of A and v of B.
+template <class F>
+__device__ __forceinline__ void segment_contacts(uint32_t segA, uint32_t stA, uint32_t fa,
+                                                 uint32_t segB, uint32_t stB, uint32_t fb,
+                                                 int dil, bool a_side, F &&f) {
+    uint32_t X, Y;
+    if (dil) {
+        X = fa & (fb | (fb << 1) | (fb >> 1));
+        Y = fb & (fa | (fa << 1) | (fa >> 1));
+    } else {
+        X = fa & fb;
+        Y = X;
+    }
+    const uint32_t pa = a_side ? ((segA & ~X) + stA) & X : 0u;
+    const uint32_t pb = ((segB & ~Y) + stB) & Y;
+    for (uint32_t e = pa | pb; e; e &= e - 1) {
+        const int u = __ffs(e) - 1;
+        if ((pa >> u) & 1u) f(u, dil ? low3(fb, u) : u);
+        if ((pb >> u) & 1u) f(dil ? low3(fa, u) : u, u);
+    }
+}
+
 // Shared-memory union-find over segments.  P[n] = key(parent) << 12 | parent,
 // where key is the brick-local index of a segment's smallest voxel, so the
 // smaller packed value is the smaller key.  A root holds its own packed id;
@@ -241,15 +287,36 @@ __device__ __forceinline__ void punion(int *P, const uint16_t *K, int a, int b, 
     }
 }
 
-template <int R> struct SmemVolMerge {
-    int P[kNodes];                // packed parent of each segment
+// Contact queue entries beyond the unused end of P (sized so that a Bernoulli
+// 0.5 volume needs one pass; a fuller queue takes further passes).
+template <int CONN> __host__ __device__ constexpr int queue_extra() {
+    return CONN == 26 ? 2816 : CONN == 18 ? 3328 : 2048;
+}
+
+// Pairs whose earlier strip's segments all have strictly smaller keys (every
+// pair but 26-connectivity's strip below in y, whose rows share z with ours).
+template <int CONN> __host__ __device__ constexpr bool key_monotone(int k) {
+    return CONN != 26 || k != 0;
+}
+
+// 18-connectivity: the same-row x +- 1 pairs of the strip below in z add only
+// contacts of segments that do not overlap (overlapping ones meet in pair 1).
+template <int CONN> __host__ __device__ constexpr bool overlap_joined(int k) {
+    return CONN == 18 && (k == 2 || k == 3);
+}
+
+template <int R, int QX> struct SmemVolMerge {
+    int P[kNodes];                // packed parent of each segment; [total, kNodes): queue
     uint16_t K[kNodes];           // brick-local index of the segment's smallest voxel
     uint32_t rows[R][kThreads];   // each strip's rows
+    uint32_t seg[kThreads];       // OR of each strip's rows
     uint32_t st[kThreads];        // segment starts of each strip
     int base[kThreads];           // rank of each strip's first segment
     uint32_t flag[kNodes / 32];   // roots whose component reaches a brick face
     int fbase[kNodes / 32];       // slot of the first flagged root of each flag word
     int warp_sums[kThreads / 32];
+    int nq;                       // queued contacts
+    uint32_t Q2[QX];              // queue entries past the unused end of P
 };
 
 __device__ __forceinline__ void brick_coords(const Geom3 &g, long long brick, int &bx, int &by,
@@ -266,7 +333,7 @@ template <int CONN>
 __global__ void __launch_bounds__(kThreads) kv_merge(VolArgs a, int *err) {
     constexpr int SY = Strip<CONN>::SY, SZ = Strip<CONN>::SZ, R = Strip<CONN>::R;
     constexpr int BYR = kStrips * SY;   // rows of a brick along y
-    __shared__ SmemVolMerge<R> sm;
+    __shared__ SmemVolMerge<R, queue_extra<CONN>()> sm;
     const Geom3 &g = a.g;
     const int t = threadIdx.x;
     const long long brick = blockIdx.x;
@@ -289,6 +356,8 @@ __global__ void __launch_bounds__(kThreads) kv_merge(VolArgs a, int *err) {
     }
     const uint32_t st = seg & ~(seg << 1);
     sm.st[t] = st;
+    sm.seg[t] = seg;
+    if (t == 0) sm.nq = 0;
     int total;
     const int base = block_excl_scan(__popc(st), sm.warp_sums, total);   // syncs
     sm.base[t] = base;
@@ -312,31 +381,91 @@ __global__ void __launch_bounds__(kThreads) kv_merge(VolArgs a, int *err) {
     for (int k = t; k < kNodes / 32; k += kThreads) sm.flag[k] = 0u;
     __syncthreads();
 
-    // unions with the earlier neighbour strips of the brick
+    // Unions with the earlier neighbour strips of the brick.  Every thread
+    // lists the contacts of its strip with each earlier neighbour strip
+    // (segment_contacts).  A segment's first contact with a strip of smaller
+    // keys is its parent link (a plain store: only this thread writes the
+    // parents of its segments here), which makes a forest whose roots are the
+    // smallest keys of their trees.  The other contacts go to a queue (the
+    // unused end of P, then Q2); after the forest is flattened, the whole
+    // block takes them in turn, one lock-free union each.  A contact that
+    // finds the queue full is listed again by a further pass: a thread's
+    // queued contacts are always a prefix of its list (the queue counter only
+    // grows), so each pass skips the ones queued before.
+    uint32_t *Q = reinterpret_cast<uint32_t *>(sm.P + total);
+    const int qcap1 = kNodes - total;
+    const int qcap = qcap1 + queue_extra<CONN>();
     int budget = kSmemHopBudget;
-    if (seg) {
+    int skip = 0;   // this thread's contacts queued by earlier passes
+    for (int pass = 0;; ++pass) {
+        int c = 0;
+        if (seg) {
+            uint32_t parented = 0;   // own segments (bit = rank - base) with a parent link
+            int la = -1, lb = -1;
 #pragma unroll
-        for (int k = 0; k < n_pairs<CONN>(); ++k) {
-            const StripPair sp = strip_pair<CONN>(k);
-            const int sy2 = sy + sp.dy, sz2 = sz + sp.dz;
-            if (sz2 < 0 || sy2 < 0 || sy2 >= kStrips) continue;
-            const int t2 = sz2 * kStrips + sy2;
-            uint32_t fa = 0, fb = 0;
+            for (int kk = 0; kk < n_pairs<CONN>(); ++kk) {
+                const int k = (kk + 1) % n_pairs<CONN>();   // pair 0 last
+                const StripPair sp = strip_pair<CONN>(k);
+                const int sy2 = sy + sp.dy, sz2 = sz + sp.dz;
+                if (sz2 < 0 || sy2 < 0 || sy2 >= kStrips) continue;
+                const int t2 = sz2 * kStrips + sy2;
+                uint32_t fa = 0, fb = 0;
 #pragma unroll
-            for (int rr = 0; rr < R; ++rr) {
-                if ((sp.ma >> rr) & 1) fa |= rows[rr];
-                if ((sp.mb >> rr) & 1) fb |= sm.rows[rr][t2];
+                for (int rr = 0; rr < R; ++rr) {
+                    if ((sp.ma >> rr) & 1) fa |= rows[rr];
+                    if ((sp.mb >> rr) & 1) fb |= sm.rows[rr][t2];
+                }
+                if (!fa || !fb) continue;
+                const uint32_t segB = sm.seg[t2], stB = sm.st[t2];
+                const int baseB = sm.base[t2];
+                segment_contacts(seg, st, fa, segB, stB, fb, sp.dil, true, [&](int u, int v) {
+                    if (overlap_joined<CONN>(k) && (((segB >> u) | (seg >> v)) & 1u)) return;
+                    const int ia = seg_rank3(base, st, u), jb = seg_rank3(baseB, stB, v);
+                    if (ia == la && jb == lb) return;
+                    la = ia;
+                    lb = jb;
+                    if (key_monotone<CONN>(k)) {
+                        const uint32_t bit = 1u << (ia - base);
+                        if (!(parented & bit)) {
+                            parented |= bit;
+                            if (pass == 0) sm.P[ia] = ((int)sm.K[jb] << kNodeBits) | jb;
+                            return;
+                        }
+                    }
+                    if (c++ < skip) return;
+                    const int q = atomicAdd(&sm.nq, 1);
+                    if (q < qcap) {
+                        const uint32_t ev = (uint32_t)ia | ((uint32_t)jb << 16);
+                        if (q < qcap1) Q[q] = ev;
+                        else sm.Q2[q - qcap1] = ev;
+                        ++skip;
+                    }
+                });
             }
-            if (!fa || !fb) continue;
-            const uint32_t st2 = sm.st[t2];
-            const int base2 = sm.base[t2];
-            touching_bits(fa, fb, sp.dil, [&](int p, int q) {
-                punion(sm.P, sm.K, base + __popc(st & le_mask(p)) - 1,
-                       base2 + __popc(st2 & le_mask(q)) - 1, budget, err);
-            });
         }
+        __syncthreads();
+        if (pass == 0) {   // flatten the forest of parent links
+            for (int round = 0; round < 64; ++round) {
+                int changed = 0;
+                for (int n = t; n < total; n += kThreads) {
+                    const int p = sm.P[n];
+                    const int gp = sm.P[p & kNodeMask];
+                    if (gp != p) { sm.P[n] = gp; changed = 1; }
+                }
+                if (!__syncthreads_or(changed)) break;
+            }
+        }
+        const int nq_all = sm.nq;
+        const int nq = min(nq_all, qcap);
+        for (int i = t; i < nq; i += kThreads) {
+            const uint32_t e = i < qcap1 ? Q[i] : sm.Q2[i - qcap1];
+            punion(sm.P, sm.K, (int)(e & 0xFFFFu), (int)(e >> 16), budget, err);
+        }
+        __syncthreads();
+        if (nq_all <= qcap) break;
+        if (t == 0) sm.nq = 0;
+        __syncthreads();
     }
-    __syncthreads();
     // every segment points at its root: read-only walks first (the forest no
     // longer changes), then, after a barrier, the stores, so that no walk sees
     // a half-rewritten parent
