@@ -46,13 +46,24 @@ static_assert(kSlotBits + kBrickBits == 33, "31-bit key in the top bits of a nod
 //   [kOffSt, kOffLab)    segment starts of each strip (the runs of its OR);
 //   [kOffLab, kOffKey)   label of each segment: 1 + the voxel index of its
 //                        root's smallest voxel, or -(slot + 1) for a border root;
-//   [kOffKey, ...)       key (smallest voxel index) of each border root.
+//   [kOffKey, kOffSeg)   key (smallest voxel index) of each border root;
+//   [kOffSeg, kOffXR)    OR of each strip's rows;
+//   [kOffXR, kOffXL)     x-face record of each strip's segment at x = 32 bx
+//                        (bricks with bx > 0), an int2: {slot | rows << 16,
+//                        key} of its root, rows = the strip's rows holding
+//                        that voxel (0: no such segment);
+//   [kOffXL, ...)        the same for the segment at x = 32 bx + 31 (bricks
+//                        with a brick to their right).
 constexpr int kOffBase = 4;
 constexpr int kOffSt = kOffBase + kThreads / 2;
 constexpr int kOffLab = kOffSt + kThreads;
 constexpr int kOffKey = kOffLab + kNodes;
-constexpr int kBrickInts = (kOffKey + kSlots + 63) & ~63;   // 256-byte multiple
+constexpr int kOffSeg = kOffKey + kSlots;
+constexpr int kOffXR = kOffSeg + kThreads;
+constexpr int kOffXL = kOffXR + 2 * kThreads;
+constexpr int kBrickInts = (kOffXL + 2 * kThreads + 63) & ~63;   // 256-byte multiple
 static_assert(kOffLab % 4 == 0, "16-byte aligned segment labels");
+static_assert(kOffXR % 2 == 0 && kOffXL % 2 == 0, "8-byte aligned x-face records");
 
 // Strip shape: every pair of voxels of the strip's rows whose x differ by at
 // most one is a neighbour pair (|dy| + |dz| <= 1 at 18, any at 26).
@@ -159,9 +170,21 @@ template <int CONN> __device__ __forceinline__ StripPair strip_pair(int k) {
 }
 
 // Whether the voxel at (x - 1, y + dy, z + dz) is a neighbour of (x, y, z).
-template <int CONN> __device__ __forceinline__ bool x_pair(int dy, int dz) {
-    const int s = (dy != 0) + (dz != 0);
-    return CONN == 26 || (CONN == 18 && s <= 1) || (CONN == 6 && s == 0);
+template <int CONN> __host__ __device__ constexpr bool x_pair(int dy, int dz) {
+    return CONN == 26 || (CONN == 18 && (dy != 0) + (dz != 0) <= 1) ||
+           (CONN == 6 && dy == 0 && dz == 0);
+}
+
+// Rows r2 of the strip at offset (dsy, dsz) (in strips) whose voxel at x - 1
+// is a neighbour of the voxel at x of row rr of a strip.
+template <int CONN> __host__ __device__ constexpr uint32_t x_rows(int dsy, int dsz, int rr) {
+    constexpr int SY = CONN == 6 ? 1 : 2, SZ = CONN == 26 ? 2 : 1;
+    uint32_t m = 0;
+    for (int r2 = 0; r2 < SY * SZ; ++r2) {
+        const int dy = dsy * SY + r2 % SY - rr % SY, dz = dsz * SZ + r2 / SY - rr / SY;
+        if (dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1 && x_pair<CONN>(dy, dz)) m |= 1u << r2;
+    }
+    return m;
 }
 
 // bits of the run of ones of a that starts at bit p
@@ -169,40 +192,6 @@ __device__ __forceinline__ uint32_t run_at(uint32_t a, int p) {
     const uint32_t rest = ~(a >> p);   // zeros of a from bit p on (ones past bit 31 - p)
     const int len = rest ? __ffs(rest) - 1 : 32;
     return (len >= 32 ? 0xFFFFFFFFu : ((1u << len) - 1u)) << p;
-}
-
-// Touching runs of two bit words a and b: voxels x and x' touch when
-// |x - x'| <= dil.  f(p, q) gets a bit p of a run of a and a bit q of a run of
-// b for a set of touching run pairs that connects all of them:
-//   dil = 0: two runs touch iff they overlap, and their overlap is one run of
-//   a & b; so the runs of a & b list every touching pair exactly once.
-//   dil = 1: each run of a is paired with the run of b holding the lowest
-//   b-voxel it touches, and each run of b with the run of a holding the lowest
-//   a-voxel it touches.  If neither rule picks a touching pair (A, B), A's pick
-//   B' lies left of B and B's pick A' left of A, A' touches B' (the intervals
-//   interleave), and induction on the position links A' with B'.
-template <class F>
-__device__ __forceinline__ void touching_bits(uint32_t a, uint32_t b, int dil, F &&f) {
-    if (!dil) {
-        const uint32_t o = a & b;
-        for (uint32_t s = o & ~(o << 1); s; s &= s - 1) {
-            const int p = __ffs(s) - 1;
-            f(p, p);
-        }
-        return;
-    }
-    for (uint32_t s = a & ~(a << 1); s; s &= s - 1) {
-        const int p = __ffs(s) - 1;
-        const uint32_t run = run_at(a, p);
-        const uint32_t hit = b & (run | (run << 1) | (run >> 1));
-        if (hit) f(p, __ffs(hit) - 1);
-    }
-    for (uint32_t s = b & ~(b << 1); s; s &= s - 1) {
-        const int q = __ffs(s) - 1;
-        const uint32_t run = run_at(b, q);
-        const uint32_t hit = a & (run | (run << 1) | (run >> 1));
-        if (hit) f(__ffs(hit) - 1, q);
-    }
 }
 
 // Rank of the segment holding bit u of a strip whose segment starts are st and
@@ -330,7 +319,7 @@ __device__ __forceinline__ void brick_coords(const Geom3 &g, long long brick, in
 // ---------------------------------------------------------------------------
 // Kernel 1: local merge of one brick.
 template <int CONN>
-__global__ void __launch_bounds__(kThreads) kv_merge(VolArgs a, int *err) {
+__global__ void __launch_bounds__(kThreads, 5) kv_merge(VolArgs a, int *err) {
     constexpr int SY = Strip<CONN>::SY, SZ = Strip<CONN>::SZ, R = Strip<CONN>::R;
     constexpr int BYR = kStrips * SY;   // rows of a brick along y
     __shared__ SmemVolMerge<R, queue_extra<CONN>()> sm;
@@ -528,17 +517,34 @@ __global__ void __launch_bounds__(kThreads) kv_merge(VolArgs a, int *err) {
     }
     reinterpret_cast<uint16_t *>(bw + kOffBase)[t] = (uint16_t)base;
     bw[kOffSt + t] = (int)st;
+    bw[kOffSeg + t] = (int)seg;
     const long long HW = (long long)g.H * g.W;
+    auto gkey = [&](int k) {   // volume index of brick-local voxel index k
+        const int lz = k / (32 * BYR), ly = (k / 32) % BYR;
+        return (int)((long long)(bz * kStrips * SZ + lz) * HW + (long long)(by * BYR + ly) * g.W +
+                     x0 + (k & 31));
+    };
+    auto slot_of = [&](int r) {   // border slot of flagged root r
+        return sm.fbase[r >> 5] + __popc(sm.flag[r >> 5] & ((1u << (r & 31)) - 1u));
+    };
+    // x-face records: the roots of the segments at the brick's first and last x
+    auto xrec = [&](int bit, int n) {
+        uint32_t m = 0;
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) m |= ((rows[rr] >> bit) & 1u) << rr;
+        if (!m) return make_int2(0, 0);
+        const int r = sm.P[n], slot = slot_of(r);
+        return slot < kSlots ? make_int2(slot | (int)(m << 16), gkey(sm.K[r])) : make_int2(0, 0);
+    };
+    if (bx > 0) reinterpret_cast<int2 *>(bw + kOffXR)[t] = xrec(0, base);
+    if (bx + 1 < g.nwg) reinterpret_cast<int2 *>(bw + kOffXL)[t] = xrec(31, base + __popc(st) - 1);
     for (int n = t; n < total; n += kThreads) {
         const int r = sm.P[n];
         const uint32_t fw = sm.flag[r >> 5];
-        const int k = sm.K[r];
-        const int lz = k / (32 * BYR), ly = (k / 32) % BYR;
-        const int key = (int)((long long)(bz * kStrips * SZ + lz) * HW +
-                              (long long)(by * BYR + ly) * g.W + x0 + (k & 31));
+        const int key = gkey(sm.K[r]);
         int v;
         if ((fw >> (r & 31)) & 1u) {
-            const int slot = sm.fbase[r >> 5] + __popc(fw & ((1u << (r & 31)) - 1u));
+            const int slot = slot_of(r);
             v = -(slot + 1);
             if (r == n && slot < kSlots) {   // the root publishes its slot
                 bw[kOffKey + slot] = key;
@@ -551,89 +557,108 @@ __global__ void __launch_bounds__(kThreads) kv_merge(VolArgs a, int *err) {
     }
 }
 
-// The brick and border slot of the segment holding bit `bit` of word w in
-// strip (gsy, gsz) (a segment on a brick face, so its root holds a slot).
-__device__ __forceinline__ bool seg_slot(const VolArgs &a, int w, int gsy, int gsz, int bit,
-                                         long long &brick, int &slot, int *err) {
-    const Geom3 &g = a.g;
-    brick = ((long long)(gsz / kStrips) * g.nby + gsy / kStrips) * g.nwg + w;
-    const int t = (gsz % kStrips) * kStrips + (gsy % kStrips);
-    const int *bw = a.bws + (size_t)brick * kBrickInts;
-    const int base = __ldcg(reinterpret_cast<const uint16_t *>(bw + kOffBase) + t);
-    const uint32_t st = (uint32_t)__ldcg(bw + kOffSt + t);
-    const int n = base + __popc(st & le_mask(bit)) - 1;
-    const int v = (n >= 0 && n < kNodes) ? __ldcg(bw + kOffLab + n) : 0;
-    if (v >= 0 || -v - 1 >= kSlots) { atomicOr(err, kErrResolve); return false; }
-    slot = -v - 1;
-    return true;
+// The face kernels read what the local merge wrote (bits, strip words, segment
+// labels, keys, x-face records) through L1: a kernel boundary separates the
+// writes from these reads and nothing changes them meanwhile.  Only the
+// global forest, which the unions change, is read from L2 (in gfind/gunion).
+
+// Global node of border slot `slot` of a brick, from the key it published.
+__device__ __forceinline__ gnode slot_node(const int *bw, long long brick, int slot) {
+    return node3(__ldg(bw + kOffKey + slot), brick, slot);
 }
 
-__device__ __forceinline__ gnode slot_node(const VolArgs &a, long long brick, int slot) {
-    return node3(__ldcg(a.bws + (size_t)brick * kBrickInts + kOffKey + slot), brick, slot);
+// A block's set of the border-root pairs it has unioned, so that each pair is
+// unioned once per block (faces repeat the same few pairs of large local
+// components many times).  Open addressing over 48-bit keys: brick << 26 |
+// slot << 15 | neighbour-brick code << 11 | slot of the other root.
+constexpr int kPairSet = 2048;
+constexpr unsigned long long kPairEmpty = ~0ull;
+
+__device__ __forceinline__ void pair_set_clear(unsigned long long *set) {
+    for (int i = threadIdx.x; i < kPairSet; i += blockDim.x) set[i] = kPairEmpty;
+}
+
+// Whether `key` was not in the set (it is now): the caller unions the pair.
+__device__ __forceinline__ bool pair_set_add(unsigned long long *set, unsigned long long key) {
+    unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 53) & (kPairSet - 1);
+    for (int probe = 0; probe < 16; ++probe) {
+        const unsigned long long v = *reinterpret_cast<volatile unsigned long long *>(set + h);
+        if (v == key) return false;
+        if (v == kPairEmpty) {
+            const unsigned long long old = atomicCAS(set + h, kPairEmpty, key);
+            if (old == kPairEmpty) return true;
+            if (old == key) return false;
+        }
+        h = (h + 1) & (kPairSet - 1);
+    }
+    return true;   // crowded: union it anyway
+}
+
+// Code of brick b2 relative to b, b2 = b + dx + dy * nwg + dz * nwg * nby with
+// dx, dy, dz in {-1, 0, 1}.
+__device__ __forceinline__ unsigned long long pair_key(long long b, int s, int dx, int dy, int dz,
+                                                       int s2) {
+    const int code = (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1);   // < 27
+    return ((unsigned long long)b << 27) | ((unsigned long long)s << 16) |
+           ((unsigned long long)code << 11) | (unsigned long long)s2;
 }
 
 // ---------------------------------------------------------------------------
-// Kernel 2a: unions across x faces.  Item i = (strip, word w >= 1): the
-// segment at voxel 32w of the strip and, for each neighbour strip, the segment
-// at x = 32w - 1 (in brick w - 1) when one of its rows holds a neighbour of a
-// voxel 32w of the strip's rows.  Consecutive neighbours of one border root
-// are unioned once.
+// Kernel 2a: unions across x faces.  Item i = (word w >= 1, strip): the
+// segment at voxel 32w of the strip (x-face record of brick w) and, for each of
+// the 3 x 3 strips around it, the segment at x = 32w - 1 (record of brick
+// w - 1) when one of its rows holds a neighbour of a voxel 32w of the strip's
+// rows.  Items run strip-fastest, so a block covers neighbouring strips of one
+// face, whose records mostly name the same few roots: each pair of border
+// roots is unioned once per block (pair_set_add), and a lane skips a
+// neighbour whose root it has just unioned.
 template <int CONN>
 __global__ void __launch_bounds__(256) kv_xfaces(VolArgs a, long long items, int *err) {
-    constexpr int SY = Strip<CONN>::SY, SZ = Strip<CONN>::SZ, R = Strip<CONN>::R;
+    constexpr int R = Strip<CONN>::R;
+    __shared__ unsigned long long pairs[kPairSet];
+    pair_set_clear(pairs);
+    __syncthreads();
     const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
     if (i >= items) return;
     const Geom3 &g = a.g;
-    const int nw1 = g.nwg - 1;
-    const int w = 1 + (int)(i % nw1);
-    const long long sidx = i / nw1;
+    const long long ns = (long long)g.nsy * g.nsz;
+    const int w = 1 + (int)(i / ns);
+    const long long sidx = i % ns;
     const int gsy = (int)(sidx % g.nsy), gsz = (int)(sidx / g.nsy);
-    uint32_t amask = 0;   // rows of the strip whose voxel 32w is set
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-        const int y = gsy * SY + rr % SY, z = gsz * SZ + rr / SY;
-        if (y < g.H && z < g.D && (__ldcg(a.bits + ((size_t)z * g.H + y) * g.nwg + w) & 1u))
-            amask |= 1u << rr;
-    }
-    if (!amask) return;
+    const long long brick = ((long long)(gsz / kStrips) * g.nby + gsy / kStrips) * g.nwg + w;
+    const int2 xr = __ldg(reinterpret_cast<const int2 *>(a.bws + (size_t)brick * kBrickInts +
+                                                          kOffXR) +
+                           (gsz % kStrips) * kStrips + gsy % kStrips);
+    const uint32_t m = (uint32_t)xr.x >> 16;
+    if (!m) return;
+    const int slot = xr.x & 0xFFFF;
+    const gnode self = node3(xr.y, brick, slot);
     const Forest3 F{a.par};
     int budget = kGlobHopBudget;
-    gnode self = kNoNode;
-    long long last_brick = -1;
-    int last_slot = -1;
+    gnode last = kNoNode;
+#pragma unroll
     for (int dsz = -1; dsz <= 1; ++dsz)
+#pragma unroll
         for (int dsy = -1; dsy <= 1; ++dsy) {
+            uint32_t near = 0;   // rows of the other strip that can hold a neighbour
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr)
+                if ((m >> rr) & 1u) near |= x_rows<CONN>(dsy, dsz, rr);
+            if (!near) continue;
             const int gsy2 = gsy + dsy, gsz2 = gsz + dsz;
             if (gsy2 < 0 || gsy2 >= g.nsy || gsz2 < 0 || gsz2 >= g.nsz) continue;
-            bool adj = false;
-#pragma unroll
-            for (int r2 = 0; r2 < R; ++r2) {
-                const int y2 = gsy2 * SY + r2 % SY, z2 = gsz2 * SZ + r2 / SY;
-                if (y2 >= g.H || z2 >= g.D) continue;
-                bool near = false;   // a set row of the strip neighbours row r2 at dx = 1
-#pragma unroll
-                for (int rr = 0; rr < R; ++rr) {
-                    const int dy = y2 - (gsy * SY + rr % SY), dz = z2 - (gsz * SZ + rr / SY);
-                    near |= ((amask >> rr) & 1u) && dy >= -1 && dy <= 1 && dz >= -1 &&
-                            dz <= 1 && x_pair<CONN>(dy, dz);
-                }
-                if (near && (__ldcg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + (w - 1)) >> 31))
-                    adj = true;
-            }
-            if (!adj) continue;
-            long long ob;
-            int os;
-            if (!seg_slot(a, w - 1, gsy2, gsz2, 31, ob, os, err)) return;
-            if (ob == last_brick && os == last_slot) continue;
-            last_brick = ob;
-            last_slot = os;
-            if (self == kNoNode) {
-                long long sb;
-                int ss;
-                if (!seg_slot(a, w, gsy, gsz, 0, sb, ss, err)) return;
-                self = slot_node(a, sb, ss);
-            }
-            gunion(F, self, slot_node(a, ob, os), budget, err);
+            const int dby = gsy2 / kStrips - gsy / kStrips, dbz = gsz2 / kStrips - gsz / kStrips;
+            const long long b2 = brick - 1 + ((long long)dbz * g.nby + dby) * g.nwg;
+            const int2 xl = __ldg(reinterpret_cast<const int2 *>(a.bws + (size_t)b2 * kBrickInts +
+                                                                  kOffXL) +
+                                   (gsz2 % kStrips) * kStrips + gsy2 % kStrips);
+            if (!(((uint32_t)xl.x >> 16) & near)) continue;
+            const int slot2 = xl.x & 0xFFFF;
+            const gnode other = node3(xl.y, b2, slot2);
+            if (other == last) continue;
+            last = other;
+            if (!pair_set_add(pairs, pair_key(brick, slot, -1, dby, dbz, slot2))) continue;
+            gunion(F, self, other, budget, err);
         }
 }
 
@@ -672,19 +697,25 @@ __device__ __forceinline__ void face_strip(long long f, int nsy, int &z, int &y)
 }
 
 // ---------------------------------------------------------------------------
-// Kernel 2b: unions across y and z faces.  Item = (face strip, strip pair k,
-// word): the touching segments of the strip and of its k-th earlier neighbour
-// strip, when that strip lies in another brick.  Consecutive pairs of the same
-// two border roots are unioned once.
+// Kernel 2b: unions across y and z faces.  Item = (word, face strip, strip pair
+// k), k fastest: the contacts of the strip and of its k-th earlier neighbour
+// strip, when that strip lies in another brick, one per segment of either strip
+// (segment_contacts).  A contact is unioned unless the lane has just unioned
+// the same two border roots or the block has (pair_set_add).
 template <int CONN>
 __global__ void __launch_bounds__(256) kv_yzfaces(VolArgs a, long long items, int *err) {
     constexpr int SY = Strip<CONN>::SY, SZ = Strip<CONN>::SZ, R = Strip<CONN>::R;
+    __shared__ unsigned long long pairs[kPairSet];
+    pair_set_clear(pairs);
+    __syncthreads();
     const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
     if (i >= items) return;
     const Geom3 &g = a.g;
-    const int w = (int)(i % g.nwg);
-    const long long fk = i / g.nwg;
-    const StripPair sp = strip_pair<CONN>((int)(fk % n_pairs<CONN>()));
+    const long long nfk = items / g.nwg;   // face strips x pairs
+    const int w = (int)(i / nfk);
+    const long long fk = i % nfk;
+    const int k = (int)(fk % n_pairs<CONN>());
+    const StripPair sp = strip_pair<CONN>(k);
     int gsy, gsz;
     face_strip(fk / n_pairs<CONN>(), g.nsy, gsz, gsy);
     const int gsy2 = gsy + sp.dy, gsz2 = gsz + sp.dz;
@@ -695,29 +726,44 @@ __global__ void __launch_bounds__(256) kv_yzfaces(VolArgs a, long long items, in
     for (int rr = 0; rr < R; ++rr) {
         const int y = gsy * SY + rr % SY, z = gsz * SZ + rr / SY;
         if (((sp.ma >> rr) & 1) && y < g.H && z < g.D)
-            fa |= __ldcg(a.bits + ((size_t)z * g.H + y) * g.nwg + w);
+            fa |= __ldg(a.bits + ((size_t)z * g.H + y) * g.nwg + w);
         const int y2 = gsy2 * SY + rr % SY, z2 = gsz2 * SZ + rr / SY;
         if (((sp.mb >> rr) & 1) && y2 < g.H && z2 < g.D)
-            fb |= __ldcg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + w);
+            fb |= __ldg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + w);
     }
     if (!fa || !fb) return;
+    const long long ba = ((long long)(gsz / kStrips) * g.nby + gsy / kStrips) * g.nwg + w;
+    const long long bb = ((long long)(gsz2 / kStrips) * g.nby + gsy2 / kStrips) * g.nwg + w;
+    const int ta = (gsz % kStrips) * kStrips + gsy % kStrips;
+    const int tb = (gsz2 % kStrips) * kStrips + gsy2 % kStrips;
+    const int *bwa = a.bws + (size_t)ba * kBrickInts, *bwb = a.bws + (size_t)bb * kBrickInts;
+    const uint32_t sega = (uint32_t)__ldg(bwa + kOffSeg + ta), sta = (uint32_t)__ldg(bwa + kOffSt + ta);
+    const uint32_t segb = (uint32_t)__ldg(bwb + kOffSeg + tb), stb = (uint32_t)__ldg(bwb + kOffSt + tb);
+    const int basea = __ldg(reinterpret_cast<const uint16_t *>(bwa + kOffBase) + ta);
+    const int baseb = __ldg(reinterpret_cast<const uint16_t *>(bwb + kOffBase) + tb);
     const Forest3 F{a.par};
     int budget = kGlobHopBudget;
     int last_sa = -1, last_sb = -1;
     bool bad = false;
-    touching_bits(fa, fb, sp.dil, [&](int p, int q) {
-        long long ba, bb;
-        int sa, sb;
+    segment_contacts(sega, sta, fa, segb, stb, fb, sp.dil, true, [&](int u, int v) {
         if (bad) return;
-        if (!seg_slot(a, w, gsy, gsz, p, ba, sa, err) ||
-            !seg_slot(a, w, gsy2, gsz2, q, bb, sb, err)) {
+        if (overlap_joined<CONN>(k) && (((segb >> u) | (sega >> v)) & 1u)) return;
+        const int na = seg_rank3(basea, sta, u), nb = seg_rank3(baseb, stb, v);
+        const int va = (na >= 0 && na < kNodes) ? __ldg(bwa + kOffLab + na) : 0;
+        const int vb = (nb >= 0 && nb < kNodes) ? __ldg(bwb + kOffLab + nb) : 0;
+        if (va >= 0 || vb >= 0 || -va - 1 >= kSlots || -vb - 1 >= kSlots) {
+            atomicOr(err, kErrResolve);
             bad = true;
             return;
         }
+        const int sa = -va - 1, sb = -vb - 1;
         if (sa == last_sa && sb == last_sb) return;
         last_sa = sa;
         last_sb = sb;
-        gunion(F, slot_node(a, ba, sa), slot_node(a, bb, sb), budget, err);
+        if (!pair_set_add(pairs, pair_key(ba, sa, 0, gsy2 / kStrips - gsy / kStrips,
+                                          gsz2 / kStrips - gsz / kStrips, sb)))
+            return;
+        gunion(F, slot_node(bwa, ba, sa), slot_node(bwb, bb, sb), budget, err);
     });
 }
 
@@ -795,28 +841,33 @@ __global__ void __launch_bounds__(kThreads) kv_link(VolArgs a, int *err) {
     }
     __syncthreads();
     // the brick's rows in raster order, 8 four-voxel chunks each: a warp stores
-    // four whole 128-byte rows
+    // four whole 128-byte rows.  Thread t keeps chunk t % 8 of one row along y
+    // through the brick's layers along z, 32 / BYR layers apart.
     const int x0 = 32 * bx;
-    for (int k = 0; k < R * 8; ++k) {
-        const int idx = k * kThreads + t;
-        const int q = idx >> 3, c = idx & 7;
-        const int ly = q % BYR, lz = q / BYR;
-        const int y = by * BYR + ly, z = bz * kStrips * SZ + lz;
-        const int xs = x0 + 4 * c;
-        if (y >= g.H || z >= g.D || xs >= g.W) continue;
-        const int ts = (lz / SZ) * kStrips + ly / SY, rr = (lz % SZ) * SY + ly % SY;
-        const uint32_t rb = sm.rows[rr][ts], sq = sm.st[ts];
-        const int b0 = sm.base[ts];
-        int v[4];
+    const int c = t & 7, q0 = t >> 3;
+    const int ly = q0 % BYR, y = by * BYR + ly, xs = x0 + 4 * c;
+    if (y >= g.H || xs >= g.W) return;
+    constexpr int kDz = (kThreads / 8) / BYR;   // layers between a thread's rows
+    static_assert(kDz * BYR == kThreads / 8, "whole layers per pass");
+    const int sy_ = ly / SY, ry = ly % SY, bit0 = 4 * c;
+    const uint32_t below = (1u << bit0) - 1u;   // bits under the chunk
+    const bool vec = a.out_aligned16 && xs + 3 < g.W;
+    const int z0 = bz * kStrips * SZ;
+    for (int lz = q0 / BYR; lz < kStrips * SZ && z0 + lz < g.D; lz += kDz) {
+        const int ts = (lz / SZ) * kStrips + sy_, rr = (lz % SZ) * SY + ry;
+        const uint32_t rb = sm.rows[rr][ts] >> bit0;
+        int v[4] = {0, 0, 0, 0};
+        if (rb & 0xFu) {
+            const uint32_t sq = sm.st[ts];
+            int n = sm.base[ts] + __popc(sq & below) - 1;   // rank before the chunk
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int bit = 4 * c + e;
-            int n = b0 + __popc(sq & le_mask(bit)) - 1;
-            n = n < 0 ? 0 : (n < kNodes ? n : kNodes - 1);
-            v[e] = ((rb >> bit) & 1u) ? sm.S[n] : 0;
+            for (int e = 0; e < 4; ++e) {
+                n += (sq >> (bit0 + e)) & 1u;
+                if ((rb >> e) & 1u) v[e] = sm.S[min((unsigned)n, (unsigned)kNodes - 1u)];
+            }
         }
-        int32_t *out = a.labels + ((size_t)z * g.H + y) * g.W + xs;
-        if (a.out_aligned16 && xs + 3 < g.W) {
+        int32_t *out = a.labels + ((size_t)(z0 + lz) * g.H + y) * g.W + xs;
+        if (vec) {
             __stcs(reinterpret_cast<int4 *>(out), make_int4(v[0], v[1], v[2], v[3]));
         } else {
 #pragma unroll
