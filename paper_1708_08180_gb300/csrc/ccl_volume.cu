@@ -52,8 +52,11 @@ static_assert(kSlotBits + kBrickBits == 33, "31-bit key in the top bits of a nod
 //                        (bricks with bx > 0), an int2: {slot | rows << 16,
 //                        key} of its root, rows = the strip's rows holding
 //                        that voxel (0: no such segment);
-//   [kOffXL, ...)        the same for the segment at x = 32 bx + 31 (bricks
-//                        with a brick to their right).
+//   [kOffXL, kOffRows)   the same for the segment at x = 32 bx + 31 (bricks
+//                        with a brick to their right);
+//   [kOffRows, ...)      the brick's rows as bits, row rr of every strip
+//                        together (R x 256 words), so that the later kernels
+//                        read them in whole 16-byte pieces.
 constexpr int kOffBase = 4;
 constexpr int kOffSt = kOffBase + kThreads / 2;
 constexpr int kOffLab = kOffSt + kThreads;
@@ -61,9 +64,12 @@ constexpr int kOffKey = kOffLab + kNodes;
 constexpr int kOffSeg = kOffKey + kSlots;
 constexpr int kOffXR = kOffSeg + kThreads;
 constexpr int kOffXL = kOffXR + 2 * kThreads;
-constexpr int kBrickInts = (kOffXL + 2 * kThreads + 63) & ~63;   // 256-byte multiple
+constexpr int kOffRows = kOffXL + 2 * kThreads;
+constexpr int kBrickInts = (kOffRows + 4 * kThreads + 63) & ~63;   // 256-byte multiple
 static_assert(kOffLab % 4 == 0, "16-byte aligned segment labels");
 static_assert(kOffXR % 2 == 0 && kOffXL % 2 == 0, "8-byte aligned x-face records");
+static_assert(kOffBase % 4 == 0 && kOffSt % 4 == 0 && kOffRows % 4 == 0,
+              "16-byte aligned strip arrays");
 
 // Strip shape: every pair of voxels of the strip's rows whose x differ by at
 // most one is a neighbour pair (|dy| + |dz| <= 1 at 18, any at 26).
@@ -108,21 +114,18 @@ inline bool dims_ok(int D, int H, int W, int conn) {
     return make_geom3(D, H, W, conn).nbricks <= kMaxBricks;
 }
 
-inline size_t bits_bytes3(const Geom3 &g) {
-    return ((size_t)g.D * g.H * g.nwg * 4u + 255u) & ~(size_t)255u;
-}
 inline size_t bricks_bytes3(const Geom3 &g) { return (size_t)g.nbricks * kBrickInts * 4u; }
 inline size_t par_bytes3(const Geom3 &g) { return (size_t)g.nbricks * kSlots * sizeof(gnode); }
 
 struct VolArgs {
     const uint8_t *vol;
     int32_t *labels;
-    uint32_t *bits;    // D*H rows x nwg words (bit k of word w = voxel 32w + k)
     int *bws;          // per-brick workspace, kBrickInts ints per brick
     gnode *par;        // global forest: kSlots parents per brick
     Geom3 g;
     int aligned16;     // volume rows start on 16-byte boundaries (W % 16 == 0)
     int out_aligned16; // label rows start on 16-byte boundaries (W % 4 == 0)
+    int out_aligned32; // label rows start on 32-byte boundaries (W % 8 == 0)
 };
 
 struct Forest3 {
@@ -511,10 +514,7 @@ __global__ void __launch_bounds__(kThreads, 5) kv_merge(VolArgs a, int *err) {
         if (nb > kSlots) atomicOr(err, kErrBorderCap);
     }
 #pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-        const int y = gsy * SY + rr % SY, z = gsz * SZ + rr / SY;
-        if (y < g.H && z < g.D) a.bits[((size_t)z * g.H + y) * g.nwg + bx] = rows[rr];
-    }
+    for (int rr = 0; rr < R; ++rr) bw[kOffRows + rr * kThreads + t] = (int)rows[rr];
     reinterpret_cast<uint16_t *>(bw + kOffBase)[t] = (uint16_t)base;
     bw[kOffSt + t] = (int)st;
     bw[kOffSeg + t] = (int)seg;
@@ -557,8 +557,8 @@ __global__ void __launch_bounds__(kThreads, 5) kv_merge(VolArgs a, int *err) {
     }
 }
 
-// The face kernels read what the local merge wrote (bits, strip words, segment
-// labels, keys, x-face records) through L1: a kernel boundary separates the
+// The face kernels read what the local merge wrote (brick rows, strip words,
+// segment labels, keys, x-face records) through L1: a kernel boundary separates the
 // writes from these reads and nothing changes them meanwhile.  Only the
 // global forest, which the unions change, is read from L2 (in gfind/gunion).
 
@@ -704,7 +704,7 @@ __device__ __forceinline__ void face_strip(long long f, int nsy, int &z, int &y)
 // the same two border roots or the block has (pair_set_add).
 template <int CONN>
 __global__ void __launch_bounds__(256) kv_yzfaces(VolArgs a, long long items, int *err) {
-    constexpr int SY = Strip<CONN>::SY, SZ = Strip<CONN>::SZ, R = Strip<CONN>::R;
+    constexpr int R = Strip<CONN>::R;
     __shared__ unsigned long long pairs[kPairSet];
     pair_set_clear(pairs);
     __syncthreads();
@@ -721,22 +721,18 @@ __global__ void __launch_bounds__(256) kv_yzfaces(VolArgs a, long long items, in
     const int gsy2 = gsy + sp.dy, gsz2 = gsz + sp.dz;
     if (gsy2 < 0 || gsy2 >= g.nsy || gsz2 < 0) return;
     if (gsy2 / kStrips == gsy / kStrips && gsz2 / kStrips == gsz / kStrips) return;
-    uint32_t fa = 0, fb = 0;
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-        const int y = gsy * SY + rr % SY, z = gsz * SZ + rr / SY;
-        if (((sp.ma >> rr) & 1) && y < g.H && z < g.D)
-            fa |= __ldg(a.bits + ((size_t)z * g.H + y) * g.nwg + w);
-        const int y2 = gsy2 * SY + rr % SY, z2 = gsz2 * SZ + rr / SY;
-        if (((sp.mb >> rr) & 1) && y2 < g.H && z2 < g.D)
-            fb |= __ldg(a.bits + ((size_t)z2 * g.H + y2) * g.nwg + w);
-    }
-    if (!fa || !fb) return;
     const long long ba = ((long long)(gsz / kStrips) * g.nby + gsy / kStrips) * g.nwg + w;
     const long long bb = ((long long)(gsz2 / kStrips) * g.nby + gsy2 / kStrips) * g.nwg + w;
     const int ta = (gsz % kStrips) * kStrips + gsy % kStrips;
     const int tb = (gsz2 % kStrips) * kStrips + gsy2 % kStrips;
     const int *bwa = a.bws + (size_t)ba * kBrickInts, *bwb = a.bws + (size_t)bb * kBrickInts;
+    uint32_t fa = 0, fb = 0;
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+        if ((sp.ma >> rr) & 1) fa |= (uint32_t)__ldg(bwa + kOffRows + rr * kThreads + ta);
+        if ((sp.mb >> rr) & 1) fb |= (uint32_t)__ldg(bwb + kOffRows + rr * kThreads + tb);
+    }
+    if (!fa || !fb) return;
     const uint32_t sega = (uint32_t)__ldg(bwa + kOffSeg + ta), sta = (uint32_t)__ldg(bwa + kOffSt + ta);
     const uint32_t segb = (uint32_t)__ldg(bwb + kOffSeg + tb), stb = (uint32_t)__ldg(bwb + kOffSt + tb);
     const int basea = __ldg(reinterpret_cast<const uint16_t *>(bwa + kOffBase) + ta);
@@ -772,10 +768,10 @@ __global__ void __launch_bounds__(256) kv_yzfaces(VolArgs a, long long items, in
 // global root and write every voxel's label.
 template <int R> struct SmemVolLink {
     __align__(16) int S[kNodes];   // label of each segment
-    int Rt[kSlots];                // final label of each border root
-    uint32_t rows[R][kThreads];
+    uint32_t rows[R][kThreads];    // the brick's rows, as in its workspace
     uint32_t st[kThreads];
-    int base[kThreads];
+    uint16_t base[kThreads];
+    int Rt[kSlots];                // final label of each border root
 };
 
 template <int CONN>
@@ -791,24 +787,32 @@ __global__ void __launch_bounds__(kThreads) kv_link(VolArgs a, int *err) {
     const int *bw = a.bws + (size_t)brick * kBrickInts;
     const int nb = min(__ldcg(bw), kSlots);
     const int nn = min(__ldcg(bw + 1), kNodes);
-    // segment labels to shared memory, 16 bytes at a time (the source is 16-byte
-    // aligned and rounding the count up stays inside the brick's workspace)
-    for (int c = t; c < (nn + 3) / 4; c += kThreads) {
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(&sm.S[4 * c]);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
-                     "l"(bw + kOffLab + 4 * c) : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    // the brick's rows, segment starts and ranks, and its segment labels, to
+    // shared memory 16 bytes at a time (every source is 16-byte aligned; the
+    // label count rounded up stays inside the brick's workspace)
     {
-        const int gsy = by * kStrips + t % kStrips, gsz = bz * kStrips + t / kStrips;
-#pragma unroll
-        for (int rr = 0; rr < R; ++rr) {
-            const int y = gsy * SY + rr % SY, z = gsz * SZ + rr / SY;
-            sm.rows[rr][t] =
-                (y < g.H && z < g.D) ? __ldcg(a.bits + ((size_t)z * g.H + y) * g.nwg + bx) : 0u;
+        auto copy16 = [&](void *dst, const int *src) {
+            const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+        };
+        constexpr int kRowChunks = R * kThreads / 4, kStChunks = kThreads / 4;
+        constexpr int kBaseChunks = kThreads / 8;
+        const int nchunks = kRowChunks + kStChunks + kBaseChunks + (nn + 3) / 4;
+        for (int c = t; c < nchunks; c += kThreads) {
+            if (c < kRowChunks) {
+                copy16(&sm.rows[0][0] + 4 * c, bw + kOffRows + 4 * c);
+            } else if (c < kRowChunks + kStChunks) {
+                const int k = c - kRowChunks;
+                copy16(&sm.st[4 * k], bw + kOffSt + 4 * k);
+            } else if (c < kRowChunks + kStChunks + kBaseChunks) {
+                const int k = c - kRowChunks - kStChunks;
+                copy16(&sm.base[8 * k], bw + kOffBase + 4 * k);
+            } else {
+                const int k = c - kRowChunks - kStChunks - kBaseChunks;
+                copy16(&sm.S[4 * k], bw + kOffLab + 4 * k);
+            }
         }
-        sm.st[t] = (uint32_t)__ldcg(bw + kOffSt + t);
-        sm.base[t] = __ldcg(reinterpret_cast<const uint16_t *>(bw + kOffBase) + t);
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
     {
         const gnode *par = a.par + (size_t)brick * kSlots;
@@ -840,38 +844,45 @@ __global__ void __launch_bounds__(kThreads) kv_link(VolArgs a, int *err) {
         }
     }
     __syncthreads();
-    // the brick's rows in raster order, 8 four-voxel chunks each: a warp stores
-    // four whole 128-byte rows.  Thread t keeps chunk t % 8 of one row along y
-    // through the brick's layers along z, 32 / BYR layers apart.
+    // the brick's rows in raster order, 4 eight-voxel chunks each: a warp
+    // stores eight whole 128-byte rows, one 32-byte store per lane where rows
+    // are 32-byte aligned.  Thread t keeps chunk t % 4 of one row along y
+    // through the brick's layers along z, 64 / BYR layers apart.
     const int x0 = 32 * bx;
-    const int c = t & 7, q0 = t >> 3;
-    const int ly = q0 % BYR, y = by * BYR + ly, xs = x0 + 4 * c;
+    const int c = t & 3, q0 = t >> 2;
+    const int ly = q0 % BYR, y = by * BYR + ly, xs = x0 + 8 * c;
     if (y >= g.H || xs >= g.W) return;
-    constexpr int kDz = (kThreads / 8) / BYR;   // layers between a thread's rows
-    static_assert(kDz * BYR == kThreads / 8, "whole layers per pass");
-    const int sy_ = ly / SY, ry = ly % SY, bit0 = 4 * c;
+    constexpr int kDz = (kThreads / 4) / BYR;   // layers between a thread's rows
+    static_assert(kDz * BYR == kThreads / 4, "whole layers per pass");
+    const int sy_ = ly / SY, ry = ly % SY, bit0 = 8 * c;
     const uint32_t below = (1u << bit0) - 1u;   // bits under the chunk
-    const bool vec = a.out_aligned16 && xs + 3 < g.W;
+    const int mode = (a.out_aligned32 && xs + 7 < g.W) ? 2 : (a.out_aligned16 && xs + 7 < g.W) ? 1 : 0;
     const int z0 = bz * kStrips * SZ;
     for (int lz = q0 / BYR; lz < kStrips * SZ && z0 + lz < g.D; lz += kDz) {
         const int ts = (lz / SZ) * kStrips + sy_, rr = (lz % SZ) * SY + ry;
         const uint32_t rb = sm.rows[rr][ts] >> bit0;
-        int v[4] = {0, 0, 0, 0};
-        if (rb & 0xFu) {
-            const uint32_t sq = sm.st[ts];
-            int n = sm.base[ts] + __popc(sq & below) - 1;   // rank before the chunk
+        int v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (rb & 0xFFu) {
+            const uint32_t sq = sm.st[ts] >> bit0;
+            int n = sm.base[ts] + __popc(sm.st[ts] & below) - 1;   // rank before the chunk
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                n += (sq >> (bit0 + e)) & 1u;
+            for (int e = 0; e < 8; ++e) {
+                n += (sq >> e) & 1u;
                 if ((rb >> e) & 1u) v[e] = sm.S[min((unsigned)n, (unsigned)kNodes - 1u)];
             }
         }
         int32_t *out = a.labels + ((size_t)(z0 + lz) * g.H + y) * g.W + xs;
-        if (vec) {
+        if (mode == 2) {
+            asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(out),
+                         "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
+                         "r"(v[6]), "r"(v[7])
+                         : "memory");
+        } else if (mode == 1) {
             __stcs(reinterpret_cast<int4 *>(out), make_int4(v[0], v[1], v[2], v[3]));
+            __stcs(reinterpret_cast<int4 *>(out) + 1, make_int4(v[4], v[5], v[6], v[7]));
         } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
+            for (int e = 0; e < 8; ++e)
                 if (xs + e < g.W) out[e] = v[e];
         }
     }
@@ -898,7 +909,7 @@ extern "C" size_t ccl_workspace_bytes3d(int depth, int height, int width, int co
     using namespace ccl::vol;
     if (!valid_conn3(connectivity) || !dims_ok(depth, height, width, connectivity)) return 0;
     const Geom3 g = make_geom3(depth, height, width, connectivity);
-    return bits_bytes3(g) + bricks_bytes3(g) + par_bytes3(g);
+    return bricks_bytes3(g) + par_bytes3(g);
 }
 
 extern "C" ccl_status ccl_label3d(const uint8_t *d_vol, int32_t *d_labels, int depth, int height,
@@ -923,12 +934,11 @@ extern "C" ccl_status ccl_label3d(const uint8_t *d_vol, int32_t *d_labels, int d
     a.g = make_geom3(depth, height, width, connectivity);
     a.vol = d_vol;
     a.labels = d_labels;
-    a.bits = static_cast<uint32_t *>(d_ws);
-    a.bws = reinterpret_cast<int *>(static_cast<char *>(d_ws) + bits_bytes3(a.g));
-    a.par = reinterpret_cast<ccl::gnode *>(static_cast<char *>(d_ws) + bits_bytes3(a.g) +
-                                           bricks_bytes3(a.g));
+    a.bws = static_cast<int *>(d_ws);
+    a.par = reinterpret_cast<ccl::gnode *>(static_cast<char *>(d_ws) + bricks_bytes3(a.g));
     a.aligned16 = (width % 16 == 0) && (reinterpret_cast<uintptr_t>(d_vol) % 16 == 0);
     a.out_aligned16 = (width % 4 == 0) && (reinterpret_cast<uintptr_t>(d_labels) % 16 == 0);
+    a.out_aligned32 = (width % 8 == 0) && (reinterpret_cast<uintptr_t>(d_labels) % 32 == 0);
     switch (connectivity) {
         case 6: launch_volume<6>(a, err, s); break;
         case 18: launch_volume<18>(a, err, s); break;
