@@ -198,7 +198,7 @@ void ccl_set_phase_events(void *const *events);
  * asynchronous CUDA error. */
 ccl_status ccl_sync(ccl_stream stream);
 
-/* Free library-owned workspaces, side streams and batched-path state on every
+/* Free library-owned workspaces and batched-path state on every
  * device, and forget the device addresses the library caches per device (its
  * error word, the scratch array of ccl_label_static).  Call it after a
  * device's context was reset (cudaDeviceReset) and before using the library

@@ -24,15 +24,6 @@ void *library_workspace(cudaStream_t stream, size_t bytes, ccl_status *st);
 // Release every library-owned workspace.
 void free_library_workspaces();
 
-// A library-owned side stream for (current device, stream), with a fork event
-// (recorded on the caller's stream, waited for by the side stream) and a join
-// event (recorded on the side stream, waited for by the caller's stream).
-struct SideStream {
-    cudaStream_t stream;
-    cudaEvent_t fork, join;
-};
-bool side_stream(cudaStream_t stream, SideStream *out);
-
 // Hop budgets the 2-D kernels are launched with (ccl_set_hop_budget).
 int hop_budget_smem();
 int hop_budget_glob();

@@ -61,19 +61,20 @@ __global__ void __launch_bounds__(kThreads, 8) k_link(ImageArgs a, int *err) {
     link_tile<NW, HS>(a, blockIdx.x, sm.S, sm.c, err);
 }
 
-// The statistics grid of ccl_label_with_stats: the per-tile statistics tables
-// and the link phase's shared memory without its label table, dynamic.
-constexpr size_t kLinkStatsSmem = ((sizeof(SmemLinkStats) + 15) & ~(size_t)15) + sizeof(SmemLinkCore);
+// The link kernel of ccl_label_with_stats: the same blocks that write the
+// labels gather every component's statistics (the per-tile statistics
+// tables and the link's shared memory, dynamic).  The statistics work
+// (shared-memory tables, register aggregation) fills issue slots that the
+// label stores, bound by HBM writes, leave free.
+constexpr size_t kLinkFusedSmem = ((sizeof(SmemLinkStats) + 15) & ~(size_t)15) + sizeof(SmemLink);
 
-// Statistics of every tile (ccl_label_with_stats), without the label image:
-// launched on a side stream so that it runs alongside the link kernel, which
-// is bound by HBM writes while this one reads only compact data.
 template <int NW, int HS>
-__global__ void __launch_bounds__(kThreads, 5) k_stats_tile(ImageArgs a, int *err) {
+__global__ void __launch_bounds__(kThreads, 4) k_link_stats(ImageArgs a, int *err) {
     extern __shared__ __align__(16) unsigned char dsm[];
     SmemLinkStats *sx = reinterpret_cast<SmemLinkStats *>(dsm);
-    SmemLinkCore &sm = *reinterpret_cast<SmemLinkCore *>(dsm + ((sizeof(SmemLinkStats) + 15) & ~(size_t)15));
-    link_tile<NW, HS, true, false>(a, blockIdx.x, nullptr, sm, err, sx);
+    SmemLink &sm = *reinterpret_cast<SmemLink *>(dsm + ((sizeof(SmemLinkStats) + 15) & ~(size_t)15));
+    pdl_launch_dependents();
+    link_tile<NW, HS, true>(a, blockIdx.x, sm.S, sm.c, err, sx);
 }
 
 // Statistics, last step: every border root that is its component's global
@@ -131,14 +132,17 @@ static void launch_merge_link(const ImageArgs &a, bool local_only, int *err, cud
             launch_pdl(km, (unsigned)ntiles, (unsigned)kThreads, s, a, local_only ? 1 : 0, err);
         else
             km<<<ntiles, kThreads, 0, s>>>(a, local_only ? 1 : 0, err);
-    } else if (stats) {   // the statistics grid (the link itself is launched separately)
+    } else if (stats) {   // labels and statistics in one grid
         static bool attr_set = false;   // per template instance; idempotent
         if (!attr_set) {
-            cudaFuncSetAttribute(k_stats_tile<NW, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kLinkStatsSmem);
+            cudaFuncSetAttribute(k_link_stats<NW, HS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kLinkFusedSmem);
             attr_set = true;
         }
-        k_stats_tile<NW, HS><<<ntiles, kThreads, kLinkStatsSmem, s>>>(a, err);
+        if (link_early)
+            launch_pdl_smem(k_link_stats<NW, HS>, (unsigned)ntiles, (unsigned)kThreads, kLinkFusedSmem, s, a, err);
+        else
+            k_link_stats<NW, HS><<<ntiles, kThreads, kLinkFusedSmem, s>>>(a, err);
     } else if (link_early) {
         launch_pdl(k_link<NW, HS>, (unsigned)ntiles, (unsigned)kThreads, s, a, err);
     } else {
@@ -289,18 +293,7 @@ ccl_status enqueue_label(const uint8_t *d_img, int32_t *d_labels, int height, in
     }
     if (timed) cudaEventRecord(t_phase_events[2], stream);
     if (so) {
-        // statistics on a side stream, alongside the link kernel; joined before
-        // the pack kernel (the event between the seam and link kernels means
-        // the link kernel does not start early here)
-        SideStream side;
-        if (!side_stream(stream, &side)) return CCL_ERR_CUDA;
-        if (cudaEventRecord(side.fork, stream) != cudaSuccess ||
-            cudaStreamWaitEvent(side.stream, side.fork, 0) != cudaSuccess)
-            return CCL_ERR_CUDA;
-        launch_tile_kernel(a, false, err, side.stream, true, false, true);
-        if (cudaEventRecord(side.join, side.stream) != cudaSuccess) return CCL_ERR_CUDA;
-        launch_tile_kernel(a, local_only, err, stream, true, false, false);
-        if (cudaStreamWaitEvent(stream, side.join, 0) != cudaSuccess) return CCL_ERR_CUDA;
+        launch_tile_kernel(a, local_only, err, stream, true, seams, true);
         k_stats_pack<<<(unsigned)(g.tiles_x * g.tiles_y), 256, 0, stream>>>(a, err);
     } else {
         launch_tile_kernel(a, local_only, err, stream, true, seams, false);

@@ -22,7 +22,6 @@ std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 std::atomic<int *> g_err_ptr[kMaxDevices];                        // device -> address
 std::map<std::pair<int, cudaStream_t>, std::pair<void *, size_t>> g_ws;  // library workspaces
-std::map<std::pair<int, cudaStream_t>, SideStream> g_side;                 // side streams
 }  // namespace
 
 int *device_error_word() {
@@ -85,36 +84,7 @@ void free_library_workspaces() {
         cudaFree(kv.second.first);
     }
     g_ws.clear();
-    for (auto &kv : g_side) {
-        cudaSetDevice(kv.first.first);
-        cudaStreamSynchronize(kv.second.stream);
-        cudaEventDestroy(kv.second.fork);
-        cudaEventDestroy(kv.second.join);
-        cudaStreamDestroy(kv.second.stream);
-    }
-    g_side.clear();
     cudaSetDevice(cur);
-}
-
-bool side_stream(cudaStream_t stream, SideStream *out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_side.find({dev, stream});
-    if (it != g_side.end()) { *out = it->second; return true; }
-    SideStream s{};
-    if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    if (cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    g_side[{dev, stream}] = s;
-    *out = s;
-    return true;
 }
 
 bool valid_image_dims(int height, int width) {

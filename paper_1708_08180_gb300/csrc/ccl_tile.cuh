@@ -788,10 +788,9 @@ __device__ __forceinline__ void seam_block(const ImageArgs &a, long long idx0, l
 // give every segment its final label (its local root's, or the resolved label
 // of its border root), and write one int32 per pixel.  The stores are laid
 // out so that 32 lanes write 128 consecutive pixels (512 bytes) of one row.
-// STATS: gather the component statistics of the tile (ccl_label_with_stats);
-// LABELS: write the label image.  The statistics run as a separate grid with
-// LABELS false, concurrently with the plain link (LABELS true, STATS false).
-template <int NW, int HS, bool STATS = false, bool LABELS = true>
+// STATS: also gather the component statistics of the tile, in the same
+// blocks (ccl_label_with_stats).
+template <int NW, int HS, bool STATS = false>
 __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, int *S, SmemLinkCore &sm,
                                           int *err, SmemLinkStats *sx = nullptr) {
     constexpr int NS = kThreads / NW;
@@ -816,7 +815,7 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, int *S, 
     // the per-segment labels, copied to shared memory asynchronously
     // (16-byte cp.async; the source starts 16 bytes into the 256-byte aligned
     // tile workspace, and rounding the count up stays inside the workspace)
-    for (int c = tid; LABELS && c < (nseg + 3) / 4; c += kThreads) {
+    for (int c = tid; c < (nseg + 3) / 4; c += kThreads) {
         const unsigned dst = (unsigned)__cvta_generic_to_shared(&S[4 * c]);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
                      "l"(tw_ + kHdrInts + 4 * c) : "memory");
@@ -893,7 +892,7 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, int *S, 
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();   // every thread's copies of S have landed
     if (total != nseg) { if (tid == 0) atomicOr(err, kErrBorderCap); }
-    for (int n = tid; LABELS && n < total; n += kThreads) {
+    for (int n = tid; n < total; n += kThreads) {
         const int v = S[n];
         if (v < 0) {
             const int j = -v - 1;
@@ -921,12 +920,13 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, int *S, 
         auto root_acc = [&](uint32_t r) {   // a global root's site
             return bacc + (size_t)(r >> kSlotBits) * g.border_cap + (int)(r & ((1u << kSlotBits) - 1u));
         };
-        // A thread adds up its pieces in registers: one accumulator for the
-        // first component it meets that crosses the tile border (in a dense
-        // image, the large component most pieces belong to) and one for the
-        // current run of pieces of any other component, flushed when the
-        // component changes.  The crossing one is flushed at the end with warp
-        // reductions among the lanes that hold the same component.
+        // A thread adds up its pieces in registers: the first component it
+        // meets that crosses the tile border (in a dense image, the large
+        // component most pieces belong to) gathers its pieces' pixel masks and
+        // takes their statistics once, from the word's rows; one accumulator
+        // holds the current run of pieces of any other component, flushed when
+        // the component changes.  The crossing one is flushed at the end with
+        // warp reductions among the lanes that hold the same component.
         struct Agg {
             int c;   // component: >= 0 inside the tile, < 0: -(1 + aggregate index)
             unsigned cnt, xmn, ymn, xmx, ymx, sx, sy;
@@ -987,6 +987,22 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, int *S, 
         Agg B = A;
         const bool has_pre = mL && (m & 1u) && base >= 1;
         const uint32_t pre = has_pre ? (m & ~(m + 1u)) : 0u;   // run continuing from the word before
+        const int xw = 32 * w, ys = s * HS;
+        // statistics of the pixels of this word's rows under `mask`
+        auto piece = [&](uint32_t mask, unsigned &cnt, unsigned &xmn, unsigned &ymn,
+                         unsigned &xmx, unsigned &ymx, unsigned &sxl, unsigned &syl) {
+            const uint32_t tt = rows[0] & mask, bb = HS == 2 ? (rows[HS - 1] & mask) : 0u;
+            const uint32_t any = tt | bb;
+            const int ct = __popc(tt), cb = __popc(bb);
+            cnt = (unsigned)(ct + cb);
+            sxl = (unsigned)(xw * (ct + cb) + bit_position_sum(tt) + bit_position_sum(bb));
+            syl = (unsigned)(ys * ct + (ys + 1) * cb);
+            xmn = (unsigned)(xw + __ffs(any) - 1);
+            xmx = (unsigned)(xw + 31 - __clz(any));
+            ymn = ct ? ys : ys + 1;
+            ymx = cb ? ys + 1 : ys;
+        };
+        uint32_t bmask = 0u;   // the pieces of B's component, gathered once
         uint32_t rem = st;
         bool pre_left = has_pre;
         int n_next = base;
@@ -1006,14 +1022,6 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, int *S, 
                 n = n_next++;
                 if (n >= total) continue;
             }
-            const uint32_t tt = rows[0] & mask, bb = HS == 2 ? (rows[HS - 1] & mask) : 0u;
-            const uint32_t any = tt | bb;
-            const int ct = __popc(tt), cb = __popc(bb), cnt = ct + cb;
-            const int xw = 32 * w, ys = s * HS;
-            const unsigned sxl = (unsigned)(xw * cnt + bit_position_sum(tt) + bit_position_sum(bb));
-            const unsigned syl = (unsigned)(ys * ct + (ys + 1) * cb);
-            const unsigned xmn = (unsigned)(xw + __ffs(any) - 1), xmx = (unsigned)(xw + 31 - __clz(any));
-            const unsigned ymn = ct ? ys : ys + 1, ymx = cb ? ys + 1 : ys;
             const unsigned cv = sx->C[n];
             int c = (int)cv;
             if (cv & kSlotBorder) {
@@ -1022,15 +1030,18 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, int *S, 
             }
             if (c < 0 && B.c == 0x7FFFFFFF) B.c = c;
             if (c == B.c) {
-                add_to(B, (unsigned)cnt, xmn, ymn, xmx, ymx, sxl, syl);
-            } else {
-                if (c != A.c) {
-                    if (A.c != 0x7FFFFFFF) flush(A);
-                    A = Agg{c, 0u, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u, 0u};
-                }
-                add_to(A, (unsigned)cnt, xmn, ymn, xmx, ymx, sxl, syl);
+                bmask |= mask;
+                continue;
             }
+            unsigned cnt, xmn, ymn, xmx, ymx, sxl, syl;
+            piece(mask, cnt, xmn, ymn, xmx, ymx, sxl, syl);
+            if (c != A.c) {
+                if (A.c != 0x7FFFFFFF) flush(A);
+                A = Agg{c, 0u, 0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u, 0u, 0u};
+            }
+            add_to(A, cnt, xmn, ymn, xmx, ymx, sxl, syl);
         }
+        if (bmask) piece(bmask, B.cnt, B.xmn, B.ymn, B.xmx, B.ymx, B.sx, B.sy);
         if (A.c != 0x7FFFFFFF) flush(A);
         {
             const bool hb = B.c != 0x7FFFFFFF;
@@ -1077,7 +1088,6 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, int *S, 
         }
     }
 
-    if (!LABELS) return;
     const int ncols = min(TW, g.W - x0);   // valid columns of this tile
     const int nrows = min(TH, g.H - y0);
     if (a.out_aligned16 && (ncols & 3) == 0) {
