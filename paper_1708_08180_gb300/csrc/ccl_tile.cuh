@@ -904,6 +904,8 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, int *S, 
             }
         }
     }
+    // statistics: each border slot's hash entry becomes its aggregate index
+    for (int j = tid; STATS && j < nb; j += kThreads) sx->HJ[j] = sx->HV[sx->HJ[j]];
     __syncthreads();
 
     if (STATS) {
@@ -1002,37 +1004,53 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, int *S, 
             ymn = ct ? ys : ys + 1;
             ymx = cb ? ys + 1 : ys;
         };
-        uint32_t bmask = 0u;   // the pieces of B's component, gathered once
-        uint32_t rem = st;
-        bool pre_left = has_pre;
-        int n_next = base;
-        while (pre_left || rem) {
+        // component of piece n (a segment rank): >= 0 inside the tile,
+        // < 0: -(1 + aggregate index) of a border root
+        auto comp_of = [&](int n) {
+            const unsigned cv = sx->C[n];
+            if (!(cv & kSlotBorder)) return (int)cv;
+            const int j = (int)(cv & (kSlotBorder - 1u));
+            return -1 - (int)sx->HJ[j < nb ? j : 0];
+        };
+        // First pass, cheap and nearly uniform across the warp: the component
+        // of every piece; B takes the first crossing one, and the start bits
+        // of the other components' pieces (bit 0 for the piece continuing
+        // from the word before) are set aside.
+        uint32_t other = 0u;
+        if (has_pre) {
+            const int c = comp_of(base - 1);
+            if (c < 0) B.c = c;
+            else other |= 1u;
+        }
+        {
+            int n = base;
+            for (uint32_t rem = st; rem; rem &= rem - 1, ++n) {
+                const uint32_t bit = rem & (0u - rem);
+                if (n >= total) { other |= bit; continue; }
+                const int c = comp_of(n);
+                if (c < 0 && B.c == 0x7FFFFFFF) B.c = c;
+                if (c != B.c) other |= bit;
+            }
+        }
+        // Second pass, over the other pieces only: their statistics, added
+        // run by run of one component; B's pixels are the word's others.
+        uint32_t omask = 0u;
+        for (uint32_t rem = other; rem; rem &= rem - 1) {
+            const int i = __ffs(rem) - 1;
             int n;
             uint32_t mask;
-            if (pre_left) {
+            if (i == 0 && has_pre) {
                 n = base - 1;
                 mask = pre;
-                pre_left = false;
             } else {
-                const int i = __ffs(rem) - 1;
-                rem &= rem - 1;
+                n = base + __popc(st & ((1u << i) - 1u));
                 const uint32_t z = ~m & (0xFFFFFFFFu << i);
                 const int end = z ? __ffs(z) - 1 : 32;
                 mask = __funnelshift_lc(0xFFFFFFFFu, 0u, (unsigned)end) & (0xFFFFFFFFu << i);
-                n = n_next++;
-                if (n >= total) continue;
             }
-            const unsigned cv = sx->C[n];
-            int c = (int)cv;
-            if (cv & kSlotBorder) {
-                const int j = (int)(cv & (kSlotBorder - 1u));
-                c = -1 - (int)sx->HV[sx->HJ[j < nb ? j : 0]];
-            }
-            if (c < 0 && B.c == 0x7FFFFFFF) B.c = c;
-            if (c == B.c) {
-                bmask |= mask;
-                continue;
-            }
+            omask |= mask;
+            if (n >= total) continue;
+            const int c = comp_of(n);
             unsigned cnt, xmn, ymn, xmx, ymx, sxl, syl;
             piece(mask, cnt, xmn, ymn, xmx, ymx, sxl, syl);
             if (c != A.c) {
@@ -1041,6 +1059,7 @@ __device__ __forceinline__ void link_tile(const ImageArgs &a, int tile, int *S, 
             }
             add_to(A, cnt, xmn, ymn, xmx, ymx, sxl, syl);
         }
+        const uint32_t bmask = B.c != 0x7FFFFFFF ? (m & ~omask) : 0u;
         if (bmask) piece(bmask, B.cnt, B.xmn, B.ymn, B.xmx, B.ymx, B.sx, B.sy);
         if (A.c != 0x7FFFFFFF) flush(A);
         {
