@@ -61,6 +61,9 @@ def test_structured_volumes(conn):
         "body_centred": (((x % 2) == (y % 2)) & ((y % 2) == (z % 2))).astype(np.uint8),
         "slabs": (z % 2 == 0).astype(np.uint8),
         "columns": ((x % 3 == 0) & (y % 3 == 0)).astype(np.uint8),
+        # 16 segments per strip row and as many contacts with every neighbour strip:
+        # the local merge's contact queue overflows and takes further passes
+        "x_stripes": (x % 2 == 0).astype(np.uint8),
         # a 3-D serpentine: every other x-row of every slice, joined at alternate ends,
         # and slices joined through one corner voxel
         "serpentine": np.zeros((d, h, w), np.uint8),
