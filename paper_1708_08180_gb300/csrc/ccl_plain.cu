@@ -9,8 +9,8 @@
 
 namespace ccl {
 
-// local-merge blocks resident per SM (shared memory: 6 x SmemMerge)
-constexpr int kMergeBlocksPerSm = 6;
+// local-merge blocks resident per SM (32 registers, shared memory: 7 x SmemMerge)
+constexpr int kMergeBlocksPerSm = 7;
 
 // SMs of the current device (cached per device)
 static int sm_count() {
@@ -39,11 +39,12 @@ static int sm_count() {
 // blocks are resident when the previous grid on the stream ends; they wait
 // for that grid (pdl_wait) before reading anything.
 template <int NW, int HS, bool STATS>
-__global__ void __launch_bounds__(kThreads) k_merge(ImageArgs a, int local_only, int *err) {
+__global__ void __launch_bounds__(kThreads, 7) k_merge(ImageArgs a, int local_only, int *err) {
     __shared__ SmemMerge sm;
+    __shared__ uint16_t lslot[STATS ? kNodeCap : 2];   // statistics: local record per root
     pdl_wait();
     pdl_launch_dependents();
-    merge_tile<NW, HS, STATS>(a, blockIdx.x, local_only != 0, sm, err);
+    merge_tile<NW, HS, STATS>(a, blockIdx.x, local_only != 0, sm, err, STATS ? lslot : nullptr);
 }
 
 __global__ void __launch_bounds__(256, 5) k_seams(ImageArgs a, long long nitems, int *err) {

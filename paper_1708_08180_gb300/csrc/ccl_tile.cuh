@@ -63,7 +63,6 @@ struct SmemMerge {
     pnode P[kNodeCap];             // parent of each segment node
     uint16_t K[kNodeCap];          // key (smallest tile-local pixel index); for a
                                    // root reaching a seam, later its border slot
-    uint32_t Q[kQueueCap];         // unions left after the forest pass: a | b << 16
     uint32_t flag[kNodeCap / 32];  // roots whose component reaches a tile seam
     uint32_t top[kThreads];        // first row of the strip, per word
     uint32_t bot[kThreads];        // last row of the strip, per word
@@ -147,7 +146,7 @@ __device__ __forceinline__ int seg_rank(int base, uint32_t st, int x) {
 //   records    global root index per seam pixel column/strip (-1: empty).
 template <int NW, int HS, bool STATS = false>
 __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool local_only,
-                                           SmemMerge &sm, int *err) {
+                                           SmemMerge &sm, int *err, uint16_t *lslot = nullptr) {
     constexpr int NS = kThreads / NW;
     constexpr int TW = 32 * NW;
     constexpr int TH = NS * HS;
@@ -181,6 +180,14 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     const int base = block_excl_scan(__popc(st), sm.warp_sums, total);   // syncs: top/bot visible
     sm.st[tid] = st;
     sm.base[tid] = base;
+    // The union queue (entries a | b << 16) lives in the unused ends of P and
+    // K, past the tile's segments: at most kQueueCap entries.
+    uint32_t *const Q1 = reinterpret_cast<uint32_t *>(sm.P + total);
+    const int cap1 = kNodeCap - total;
+    const int tot2 = (total + 1) & ~1;
+    uint32_t *const Q2 = reinterpret_cast<uint32_t *>(sm.K + tot2);
+    const int qcap = min(cap1 + (kNodeCap - tot2) / 2, kQueueCap);
+    auto qat = [&](int i) -> uint32_t & { return i < cap1 ? Q1[i] : Q2[i - cap1]; };
 
     // ---- nodes: parent = self, key = smallest tile-local pixel index ----
     {
@@ -253,7 +260,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
                 const int old = atomicCAS(&sm.P[rb], (pnode)rb, (pnode)ra);
                 if (old != rb && old != ra) {
                     const int q = atomicAdd(&sm.nq, 1);
-                    if (q < kQueueCap) sm.Q[q] = (uint32_t)ra | ((uint32_t)old << 16);
+                    if (q < qcap) qat(q) = (uint32_t)ra | ((uint32_t)old << 16);
                     else sunion(sm.P, sm.K, ra, old, budget, err);   // queue full: now
                 }
             };
@@ -314,7 +321,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     // that loses a race is queued again with the loser's new parent.  (4) The
     // few pairs that lost run as lock-free unions with finds (path halving).
     constexpr int kPer = kQueueCap / kThreads;   // queue entries per thread
-    const int nq0 = min(sm.nq, kQueueCap);       // block-uniform: read after a barrier
+    const int nq0 = min(sm.nq, qcap);            // block-uniform: read after a barrier
     if (nq0 > 0) {
         const int kn = (nq0 + kThreads - 1) / kThreads;   // entries per thread (block-uniform)
         uint32_t e[kPer];
@@ -322,7 +329,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         for (int k = 0; k < kPer; ++k) {
             if (k >= kn) break;
             const int i = tid + k * kThreads;
-            e[k] = i < nq0 ? sm.Q[i] : 0xFFFFFFFFu;
+            e[k] = i < nq0 ? qat(i) : 0xFFFFFFFFu;
         }
         __syncthreads();
         if (tid == 0) sm.nq = 0;
@@ -337,14 +344,14 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             const int old = atomicCAS(&sm.P[pb], (pnode)pb, (pnode)pa);   // hook root pb under pa
             if (old != pb && old != pa) {
                 const int q = atomicAdd(&sm.nq, 1);
-                if (q < kQueueCap) sm.Q[q] = (uint32_t)pa | ((uint32_t)old << 16);
+                if (q < qcap) qat(q) = (uint32_t)pa | ((uint32_t)old << 16);
                 else sunion(sm.P, sm.K, pa, old, budget, err);   // queue full: now
             }
         }
         __syncthreads();
-        const int nq1 = min(sm.nq, kQueueCap);
+        const int nq1 = min(sm.nq, qcap);
         for (int i = tid; i < nq1; i += kThreads) {
-            const uint32_t q = sm.Q[i];
+            const uint32_t q = qat(i);
             sunion(sm.P, sm.K, (int)(q & 0xFFFFu), (int)(q >> 16), budget, err);
         }
         __syncthreads();
@@ -458,7 +465,6 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         // (a slot in a range reserved with one atomic per tile) holding its
         // label; each segment also stores its component's slot, local (>= 0)
         // or border (-(1 + border slot)), for the link phase.
-        uint16_t *lslot = reinterpret_cast<uint16_t *>(sm.Q);   // the union queue is dead here
         if (tid == 0) sm.nlocal = 0;
         __syncthreads();
         for (int n = tid; n < total; n += kThreads)
