@@ -209,7 +209,11 @@ __device__ __forceinline__ int low3(uint32_t v, int u) {
 }
 
 // Contacts of two neighbouring strips A and B at the level of their segments
-// (the runs of each strip's OR).  Facing rows fa, fb, x reach dil.  For every
+// (the runs of each strip's OR).  Facing rows fa, fb, x reach dil.  When x must
+// match (dil = 0), two segments touch exactly when they overlap, every run of
+// fa & fb lies in one segment of each strip, and so the runs of fa & fb, one
+// contact each at the run's first voxel, are the touching pairs (fewer than
+// the picks below when the rows are sparse).  Otherwise, for every
 // segment of A that touches B, its pick is the segment of B holding the lowest
 // B voxel it touches; that voxel lies within one of the segment's lowest
 // touching voxel, which the carry of (segA & ~X) + stA marks (X = the voxels
@@ -223,21 +227,23 @@ __device__ __forceinline__ int low3(uint32_t v, int u) {
 template <class F>
 __device__ __forceinline__ void segment_contacts(uint32_t segA, uint32_t stA, uint32_t fa,
                                                  uint32_t segB, uint32_t stB, uint32_t fb,
-                                                 int dil, bool a_side, F &&f) {
-    uint32_t X, Y;
-    if (dil) {
-        X = fa & (fb | (fb << 1) | (fb >> 1));
-        Y = fb & (fa | (fa << 1) | (fa >> 1));
-    } else {
-        X = fa & fb;
-        Y = X;
+                                                 int dil, F &&f) {
+    if (!dil) {
+        const uint32_t o = fa & fb;
+        for (uint32_t e = o & ~(o << 1); e; e &= e - 1) {
+            const int u = __ffs(e) - 1;
+            f(u, u);
+        }
+        return;
     }
-    const uint32_t pa = a_side ? ((segA & ~X) + stA) & X : 0u;
+    const uint32_t X = fa & (fb | (fb << 1) | (fb >> 1));
+    const uint32_t Y = fb & (fa | (fa << 1) | (fa >> 1));
+    const uint32_t pa = ((segA & ~X) + stA) & X;
     const uint32_t pb = ((segB & ~Y) + stB) & Y;
     for (uint32_t e = pa | pb; e; e &= e - 1) {
         const int u = __ffs(e) - 1;
-        if ((pa >> u) & 1u) f(u, dil ? low3(fb, u) : u);
-        if ((pb >> u) & 1u) f(dil ? low3(fa, u) : u, u);
+        if ((pa >> u) & 1u) f(u, low3(fb, u));
+        if ((pb >> u) & 1u) f(low3(fa, u), u);
     }
 }
 
@@ -410,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 5) kv_merge(VolArgs a, int *err) {
                 if (!fa || !fb) continue;
                 const uint32_t segB = sm.seg[t2], stB = sm.st[t2];
                 const int baseB = sm.base[t2];
-                segment_contacts(seg, st, fa, segB, stB, fb, sp.dil, true, [&](int u, int v) {
+                segment_contacts(seg, st, fa, segB, stB, fb, sp.dil, [&](int u, int v) {
                     if (overlap_joined<CONN>(k) && (((segB >> u) | (seg >> v)) & 1u)) return;
                     const int ia = seg_rank3(base, st, u), jb = seg_rank3(baseB, stB, v);
                     if (ia == la && jb == lb) return;
@@ -741,7 +747,7 @@ __global__ void __launch_bounds__(256) kv_yzfaces(VolArgs a, long long items, in
     int budget = kGlobHopBudget;
     int last_sa = -1, last_sb = -1;
     bool bad = false;
-    segment_contacts(sega, sta, fa, segb, stb, fb, sp.dil, true, [&](int u, int v) {
+    segment_contacts(sega, sta, fa, segb, stb, fb, sp.dil, [&](int u, int v) {
         if (bad) return;
         if (overlap_joined<CONN>(k) && (((segb >> u) | (sega >> v)) & 1u)) return;
         const int na = seg_rank3(basea, sta, u), nb = seg_rank3(baseb, stb, v);
