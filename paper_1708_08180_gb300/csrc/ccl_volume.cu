@@ -9,15 +9,18 @@
 //     16 x 16 strips; thread t of a block owns strip (t % 16, t / 16).
 //   * local merge (Kernel 1, §II-A): a block joins the segments of its brick in
 //     shared memory, each strip with its earlier neighbour strips through the
-//     rows that face each other: one contact per segment of either strip,
-//     first contacts as parent links, the other contacts queued and unioned
-//     by the whole block;
-//   * boundary analysis (Kernel 2, §II-B): threads over the rows and strips that
-//     meet a brick face union the segments that touch across it, in a global
-//     forest over the bricks' border roots (one kernel for the x faces, one for
-//     y and z);
-//   * link (§II-C): a block per brick resolves its border roots and writes the
-//     final labels, four voxels per 16-byte store, a warp covering four rows.
+//     rows that face each other: contacts listed per segment (or per overlap
+//     run where x must match), first contacts as parent links, the other
+//     contacts queued and unioned by the whole block; it also writes the
+//     brick's rows and each strip's x-face records to the brick's workspace;
+//   * boundary analysis (Kernel 2, §II-B): threads over the strips that meet a
+//     brick face union the segments that touch across it, in a global forest
+//     over the bricks' border roots (one kernel for the x faces, from the
+//     records; one for y and z, from the rows), each block unioning a pair of
+//     border roots once;
+//   * link (§II-C): a block per brick copies its rows and segment labels to
+//     shared memory, resolves its border roots and writes the final labels,
+//     eight voxels per lane in one 32-byte store, a warp covering eight rows.
 // The result is the canonical labelling: 0 for background, 1 + the smallest
 // voxel index (z*H + y)*W + x of the component.
 #include "ccl_core.cuh"
