@@ -306,6 +306,23 @@ template <int CONN> __host__ __device__ constexpr bool overlap_joined(int k) {
     return CONN == 18 && (k == 2 || k == 3);
 }
 
+// The contacts such a pair adds: a voxel u of A's facing row outside every
+// segment of B and a voxel v = u +- 1 of B's facing row outside every segment
+// of A.  Any other contact of the pair has u or v inside a segment of the
+// other strip, hence its two segments overlap (adjacent bits lie in one
+// segment) and pair 1 joins them.  f(u, v) as in segment_contacts.
+template <class F>
+__device__ __forceinline__ void diagonal_contacts(uint32_t segA, uint32_t fa, uint32_t segB,
+                                                  uint32_t fb, F &&f) {
+    const uint32_t g = fb & ~segA;
+    const uint32_t gl = g << 1, gr = g >> 1;   // bit u: g holds u - 1, u + 1
+    for (uint32_t e = fa & ~segB & (gl | gr); e; e &= e - 1) {
+        const int u = __ffs(e) - 1;
+        if ((gl >> u) & 1u) f(u, u - 1);
+        if ((gr >> u) & 1u) f(u, u + 1);
+    }
+}
+
 template <int R, int QX> struct SmemVolMerge {
     int P[kNodes];                // packed parent of each segment; [total, kNodes): queue
     uint16_t K[kNodes];           // brick-local index of the segment's smallest voxel
@@ -419,8 +436,7 @@ __global__ void __launch_bounds__(kThreads, 5) kv_merge(VolArgs a, int *err) {
                 if (!fa || !fb) continue;
                 const uint32_t segB = sm.seg[t2], stB = sm.st[t2];
                 const int baseB = sm.base[t2];
-                segment_contacts(seg, st, fa, segB, stB, fb, sp.dil, [&](int u, int v) {
-                    if (overlap_joined<CONN>(k) && (((segB >> u) | (seg >> v)) & 1u)) return;
+                auto contact = [&](int u, int v) {
                     const int ia = seg_rank3(base, st, u), jb = seg_rank3(baseB, stB, v);
                     if (ia == la && jb == lb) return;
                     la = ia;
@@ -441,7 +457,9 @@ __global__ void __launch_bounds__(kThreads, 5) kv_merge(VolArgs a, int *err) {
                         else sm.Q2[q - qcap1] = ev;
                         ++skip;
                     }
-                });
+                };
+                if (overlap_joined<CONN>(k)) diagonal_contacts(seg, fa, segB, fb, contact);
+                else segment_contacts(seg, st, fa, segB, stB, fb, sp.dil, contact);
             }
         }
         __syncthreads();
@@ -750,9 +768,8 @@ __global__ void __launch_bounds__(256) kv_yzfaces(VolArgs a, long long items, in
     int budget = kGlobHopBudget;
     int last_sa = -1, last_sb = -1;
     bool bad = false;
-    segment_contacts(sega, sta, fa, segb, stb, fb, sp.dil, [&](int u, int v) {
+    auto contact = [&](int u, int v) {
         if (bad) return;
-        if (overlap_joined<CONN>(k) && (((segb >> u) | (sega >> v)) & 1u)) return;
         const int na = seg_rank3(basea, sta, u), nb = seg_rank3(baseb, stb, v);
         const int va = (na >= 0 && na < kNodes) ? __ldg(bwa + kOffLab + na) : 0;
         const int vb = (nb >= 0 && nb < kNodes) ? __ldg(bwb + kOffLab + nb) : 0;
@@ -769,7 +786,9 @@ __global__ void __launch_bounds__(256) kv_yzfaces(VolArgs a, long long items, in
                                           gsz2 / kStrips - gsz / kStrips, sb)))
             return;
         gunion(F, slot_node(bwa, ba, sa), slot_node(bwb, bb, sb), budget, err);
-    });
+    };
+    if (overlap_joined<CONN>(k)) diagonal_contacts(sega, fa, segb, fb, contact);
+    else segment_contacts(sega, sta, fa, segb, stb, fb, sp.dil, contact);
 }
 
 // ---------------------------------------------------------------------------
