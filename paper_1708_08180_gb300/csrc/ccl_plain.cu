@@ -9,9 +9,9 @@
 
 namespace ccl {
 
-// local-merge blocks resident per SM (32 registers, shared memory: 7 x SmemMerge;
+// local-merge blocks resident per SM (32 registers, shared memory: 8 x SmemMerge;
 // the statistics variant, with a per-node record buffer, holds 6)
-constexpr int kMergeBlocksPerSm = 7;
+constexpr int kMergeBlocksPerSm = 8;
 
 // SMs of the current device (cached per device)
 static int sm_count() {
@@ -40,7 +40,7 @@ static int sm_count() {
 // blocks are resident when the previous grid on the stream ends; they wait
 // for that grid (pdl_wait) before reading anything.
 template <int NW, int HS, bool STATS>
-__global__ void __launch_bounds__(kThreads, STATS ? 6 : 7) k_merge(ImageArgs a, int local_only, int *err) {
+__global__ void __launch_bounds__(kThreads, STATS ? 6 : 8) k_merge(ImageArgs a, int local_only, int *err) {
     __shared__ SmemMerge sm;
     __shared__ uint16_t lslot[STATS ? kNodeCap : 2];   // statistics: local record per root
     pdl_wait();

@@ -65,9 +65,10 @@ struct SmemMerge {
                                    // root reaching a seam, later its border slot
     uint32_t flag[kNodeCap / 32];  // roots whose component reaches a tile seam
     uint32_t top[kThreads];        // first row of the strip, per word
-    uint32_t bot[kThreads];        // last row of the strip, per word
-    uint32_t st[kThreads];         // segment starts, per word
-    int base[kThreads];            // rank of the first segment starting in the word
+    uint32_t bot[kThreads];        // last row of the strip, per word (a word's segment
+                                   // starts follow from these two words and the word's
+                                   // left neighbour's)
+    uint16_t base[kThreads];       // rank of the first segment starting in the word
     int warp_sums[kThreads / 32];
     int nborder;
     int nq;
@@ -178,8 +179,13 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
     const uint32_t st = m & ~((m << 1) | mL);
     int total;
     const int base = block_excl_scan(__popc(st), sm.warp_sums, total);   // syncs: top/bot visible
-    sm.st[tid] = st;
-    sm.base[tid] = base;
+    sm.base[tid] = (uint16_t)base;
+    // segment starts of word o (strip o / NW, word o % NW)
+    auto st_of = [&](int o) {
+        const uint32_t mo = sm.top[o] | sm.bot[o];
+        const uint32_t ml = (o % NW) ? ((sm.top[o - 1] | sm.bot[o - 1]) >> 31) : 0u;
+        return mo & ~((mo << 1) | ml);
+    };
     // The union queue (entries a | b << 16) lives in the unused ends of P and
     // K, past the tile's segments: at most kQueueCap entries.
     uint32_t *const Q1 = reinterpret_cast<uint32_t *>(sm.P + total);
@@ -251,7 +257,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             const uint32_t aL = w > 0 ? (sm.bot[up - 1] >> 31) : 0u;
             const uint32_t bL = w > 0 ? (sm.top[tid - 1] >> 31) : 0u;
             const int baseA = sm.base[up];
-            const uint32_t stA = sm.st[up];
+            const uint32_t stA = st_of(up);
             int la = -1, lb = -1;
             auto contact = [&](int ra, int rb) {
                 if (ra == la && rb == lb) return;
@@ -274,7 +280,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
             if (HS == 2) {
                 const uint32_t aR = w < NW - 1 ? (sm.bot[up + 1] & 1u) : 0u;
                 const uint32_t bR = w < NW - 1 ? (sm.top[tid + 1] & 1u) : 0u;
-                const uint32_t stA_next0 = w < NW - 1 ? (sm.st[up + 1] & 1u) : 0u;
+                const uint32_t stA_next0 = w < NW - 1 ? (st_of(up + 1) & 1u) : 0u;
                 // b-run starts at x right after an a-run that ends at x-1
                 uint32_t dr = bv & ~av & ~((bv << 1) | bL) & ((av << 1) | aL);
                 // b-run ends at x right before an a-run that starts at x+1
@@ -407,14 +413,14 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         {   // top: strip 0
             const int o = wc;
             if ((sm.top[o] | sm.bot[o]) >> b & 1u) {
-                r_top = sm.P[seg_rank(sm.base[o], sm.st[o], b)];
+                r_top = sm.P[seg_rank(sm.base[o], st_of(o), b)];
                 if (has_up && !local_only && ((sm.top[o] >> b) & 1u)) mark(r_top);
             }
         }
         {   // bottom: strip NS-1
             const int o = (NS - 1) * NW + wc;
             if ((sm.top[o] | sm.bot[o]) >> b & 1u) {
-                r_bot = sm.P[seg_rank(sm.base[o], sm.st[o], b)];
+                r_bot = sm.P[seg_rank(sm.base[o], st_of(o), b)];
                 if (has_down && !local_only && ((sm.bot[o] >> b) & 1u)) mark(r_bot);
             }
         }
@@ -430,7 +436,7 @@ __device__ __forceinline__ void merge_tile(const ImageArgs &a, int tile, bool lo
         {   // right: column TW-1 of strip tid
             const int o = tid * NW + NW - 1;
             if ((sm.top[o] | sm.bot[o]) >> 31) {
-                r_right = sm.P[seg_rank(sm.base[o], sm.st[o], 31)];
+                r_right = sm.P[seg_rank(sm.base[o], st_of(o), 31)];
                 if (has_right && !local_only) mark(r_right);
             }
         }
