@@ -57,9 +57,12 @@ static_assert(kSlotBits + kBrickBits == 33, "31-bit key in the top bits of a nod
 //                        that voxel (0: no such segment);
 //   [kOffXL, kOffRows)   the same for the segment at x = 32 bx + 31 (bricks
 //                        with a brick to their right);
-//   [kOffRows, ...)      the brick's rows as bits, row rr of every strip
+//   [kOffRows, kOffUni)  the brick's rows as bits, row rr of every strip
 //                        together (R x 256 words), so that the later kernels
-//                        read them in whole 16-byte pieces.
+//                        read them in whole 16-byte pieces;
+//   [kOffUni, ...)       per strip (18 and 26), the border slot of the root all
+//                        its segments share, or -1 (no segment, several roots,
+//                        not a face strip).
 constexpr int kOffBase = 4;
 constexpr int kOffSt = kOffBase + kThreads / 2;
 constexpr int kOffLab = kOffSt + kThreads;
@@ -68,7 +71,8 @@ constexpr int kOffSeg = kOffKey + kSlots;
 constexpr int kOffXR = kOffSeg + kThreads;
 constexpr int kOffXL = kOffXR + 2 * kThreads;
 constexpr int kOffRows = kOffXL + 2 * kThreads;
-constexpr int kBrickInts = (kOffRows + 4 * kThreads + 63) & ~63;   // 256-byte multiple
+constexpr int kOffUni = kOffRows + 4 * kThreads;
+constexpr int kBrickInts = (kOffUni + kThreads + 63) & ~63;   // 256-byte multiple
 static_assert(kOffLab % 4 == 0, "16-byte aligned segment labels");
 static_assert(kOffXR % 2 == 0 && kOffXL % 2 == 0, "8-byte aligned x-face records");
 static_assert(kOffBase % 4 == 0 && kOffSt % 4 == 0 && kOffRows % 4 == 0,
@@ -299,6 +303,11 @@ template <int CONN> __host__ __device__ constexpr int queue_extra() {
 template <int CONN> __host__ __device__ constexpr bool key_monotone(int k) {
     return CONN != 26 || k != 0;
 }
+
+// Whether the merge records each face strip's single border slot (most face
+// strips have one at 18 and 26; about 40 % at 6 in a Bernoulli 0.5 volume, too
+// few to pay for the record).
+template <int CONN> __host__ __device__ constexpr bool uniform_slots() { return CONN != 6; }
 
 // 18-connectivity: the same-row x +- 1 pairs of the strip below in z add only
 // contacts of segments that do not overlap (overlapping ones meet in pair 1).
@@ -565,6 +574,19 @@ __global__ void __launch_bounds__(kThreads, 5) kv_merge(VolArgs a, int *err) {
     };
     if (bx > 0) reinterpret_cast<int2 *>(bw + kOffXR)[t] = xrec(0, base);
     if (bx + 1 < g.nwg) reinterpret_cast<int2 *>(bw + kOffXL)[t] = xrec(31, base + __popc(st) - 1);
+    if (uniform_slots<CONN>()) {   // a face strip's single border slot, if it has one
+        int uni = -1;
+        if (seg && yzface) {
+            const int r0 = sm.P[base];
+            bool same = true;
+            for (int n = base + 1; n < base + __popc(st); ++n) same &= sm.P[n] == r0;
+            if (same && ((sm.flag[r0 >> 5] >> (r0 & 31)) & 1u)) {
+                const int slot = slot_of(r0);
+                if (slot < kSlots) uni = slot;
+            }
+        }
+        bw[kOffUni + t] = uni;
+    }
     for (int n = t; n < total; n += kThreads) {
         const int r = sm.P[n];
         const uint32_t fw = sm.flag[r >> 5];
@@ -728,7 +750,9 @@ __device__ __forceinline__ void face_strip(long long f, int nsy, int &z, int &y)
 // k), k fastest: the contacts of the strip and of its k-th earlier neighbour
 // strip, when that strip lies in another brick, one per segment of either strip
 // (segment_contacts).  A contact is unioned unless the lane has just unioned
-// the same two border roots or the block has (pair_set_add).
+// the same two border roots or the block has (pair_set_add).  When all
+// segments of both strips share one root each (the merge records that per
+// strip), the item needs only to know whether the strips touch.
 template <int CONN>
 __global__ void __launch_bounds__(256) kv_yzfaces(VolArgs a, long long items, int *err) {
     constexpr int R = Strip<CONN>::R;
@@ -753,6 +777,8 @@ __global__ void __launch_bounds__(256) kv_yzfaces(VolArgs a, long long items, in
     const int ta = (gsz % kStrips) * kStrips + gsy % kStrips;
     const int tb = (gsz2 % kStrips) * kStrips + gsy2 % kStrips;
     const int *bwa = a.bws + (size_t)ba * kBrickInts, *bwb = a.bws + (size_t)bb * kBrickInts;
+    const int ua = uniform_slots<CONN>() ? __ldg(bwa + kOffUni + ta) : -1;
+    const int ub = uniform_slots<CONN>() ? __ldg(bwb + kOffUni + tb) : -1;
     uint32_t fa = 0, fb = 0;
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) {
@@ -760,31 +786,42 @@ __global__ void __launch_bounds__(256) kv_yzfaces(VolArgs a, long long items, in
         if ((sp.mb >> rr) & 1) fb |= (uint32_t)__ldg(bwb + kOffRows + rr * kThreads + tb);
     }
     if (!fa || !fb) return;
+    const int dyb = gsy2 / kStrips - gsy / kStrips, dzb = gsz2 / kStrips - gsz / kStrips;
+    const Forest3 F{a.par};
+    int budget = kGlobHopBudget;
+    if (ua >= 0 && ub >= 0) {   // every contact joins the same two border roots: is there one?
+        const uint32_t touch = sp.dil ? fa & (fb | (fb << 1) | (fb >> 1)) : fa & fb;
+        if (touch && pair_set_add(pairs, pair_key(ba, ua, 0, dyb, dzb, ub)))
+            gunion(F, slot_node(bwa, ba, ua), slot_node(bwb, bb, ub), budget, err);
+        return;
+    }
     const uint32_t sega = (uint32_t)__ldg(bwa + kOffSeg + ta), sta = (uint32_t)__ldg(bwa + kOffSt + ta);
     const uint32_t segb = (uint32_t)__ldg(bwb + kOffSeg + tb), stb = (uint32_t)__ldg(bwb + kOffSt + tb);
     const int basea = __ldg(reinterpret_cast<const uint16_t *>(bwa + kOffBase) + ta);
     const int baseb = __ldg(reinterpret_cast<const uint16_t *>(bwb + kOffBase) + tb);
-    const Forest3 F{a.par};
-    int budget = kGlobHopBudget;
     int last_sa = -1, last_sb = -1;
     bool bad = false;
+    // the border slot of the segment holding voxel x of a strip (its single
+    // slot when the strip has one), or -1 after flagging a missing slot
+    auto slot_at = [&](int uni, const int *bw, int base, uint32_t st, int x) {
+        if (uni >= 0) return uni;
+        const int n = seg_rank3(base, st, x);
+        const int v = (n >= 0 && n < kNodes) ? __ldg(bw + kOffLab + n) : 0;
+        if (v >= 0 || -v - 1 >= kSlots) return -1;
+        return -v - 1;
+    };
     auto contact = [&](int u, int v) {
         if (bad) return;
-        const int na = seg_rank3(basea, sta, u), nb = seg_rank3(baseb, stb, v);
-        const int va = (na >= 0 && na < kNodes) ? __ldg(bwa + kOffLab + na) : 0;
-        const int vb = (nb >= 0 && nb < kNodes) ? __ldg(bwb + kOffLab + nb) : 0;
-        if (va >= 0 || vb >= 0 || -va - 1 >= kSlots || -vb - 1 >= kSlots) {
+        const int sa = slot_at(ua, bwa, basea, sta, u), sb = slot_at(ub, bwb, baseb, stb, v);
+        if (sa < 0 || sb < 0) {
             atomicOr(err, kErrResolve);
             bad = true;
             return;
         }
-        const int sa = -va - 1, sb = -vb - 1;
         if (sa == last_sa && sb == last_sb) return;
         last_sa = sa;
         last_sb = sb;
-        if (!pair_set_add(pairs, pair_key(ba, sa, 0, gsy2 / kStrips - gsy / kStrips,
-                                          gsz2 / kStrips - gsz / kStrips, sb)))
-            return;
+        if (!pair_set_add(pairs, pair_key(ba, sa, 0, dyb, dzb, sb))) return;
         gunion(F, slot_node(bwa, ba, sa), slot_node(bwb, bb, sb), budget, err);
     };
     if (overlap_joined<CONN>(k)) diagonal_contacts(sega, fa, segb, fb, contact);
